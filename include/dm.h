@@ -1,0 +1,181 @@
+/*
+ * dm.h -- C ABI of the GB300 multi-mode difference-map (DM) ptychography
+ * library.
+ *
+ * One DM iteration (arXiv 1808.10375, Sec. II) over all views j and probe
+ * modes k, with one object mode:
+ *   Eq. 3   psi_j^k <- psi_j^k + beta ( F^-1 F_c[2 P_k O - psi_j^k] - P_k O )
+ *           where F_c rescales every mode of its argument's transform by
+ *           sqrt(I_j(q) / sum_k |F[.]_k(q)|^2), keeping the phase;
+ *   Eq. 5   O(r)   <- sum_jk conj(P_k(r-r_j)) psi_j^k(r-r_j) / sum_jk |P_k(r-r_j)|^2
+ *   Eq. 4   P_k(u) <- sum_j conj(O(r_j+u)) psi_j^k(u) / sum_j |O(r_j+u)|^2
+ *   Eq. 6   relative change of O and of each P_k between iterations.
+ *
+ * Conventions fixed by this library (the paper leaves them open):
+ *  - F is the orthonormal 2-D DFT with the zero frequency at [0][0]; where
+ *    sum_k |F[.]_k(q)|^2 is zero the projected field is zero; negative
+ *    intensities are rejected at dm_init.
+ *  - Eq. 5 is applied first (with the probe the Fourier step used), then
+ *    Eq. 4 with the new object (Gauss-Seidel), n_inner times per iteration.
+ *  - Each overlap denominator gets delta = denom_floor_rel * max(denominator);
+ *    object pixels that no view covers keep their value.
+ *  - The Fourier error is E_F = sqrt(sum_jq (sqrt(S_j(q)) - sqrt(I_j(q)))^2 /
+ *    sum_jq I_j(q)), S_j the mode sum of the Fourier step.
+ *
+ * Layouts (all row-major, complex = interleaved float pairs (re, im)):
+ *   positions    int32  [J][2]        top-left (row, col) of each N x N footprint,
+ *                                     0 <= row <= obj_h - N, 0 <= col <= obj_w - N
+ *   intensities  float  [J][N][N]     recorded I_j(q), q = (qy, qx), DC at [0][0]
+ *   probe        float  [M][N][N][2]  probe modes P_k(u)
+ *   object       float  [H][W][2]     object O(r)
+ *   exit waves   float  [J][M][N][N][2]
+ *
+ * Memory: every pointer argument is a host pointer when its mem_kind is
+ * DM_HOST and a device pointer (on the context's device) when DM_DEVICE.
+ * Inputs are copied at the call; the caller keeps ownership of every buffer
+ * it passes.  All device memory the context needs is obtained once in
+ * dm_init, through params->alloc (if non-NULL) or cudaMallocAsync on the
+ * context's stream, and released by dm_free.
+ *
+ * Streams and synchronisation: all work is enqueued on params->stream (or a
+ * stream the library creates when it is NULL).  dm_iterate only enqueues;
+ * errors raised on the device (non-finite metrics, expired bounded waits)
+ * are reported by the next call that synchronises: dm_sync, dm_get_*.
+ *
+ * Errors: every int-returning call returns DM_OK (0) or a negative DM_E*
+ * code and never aborts; dm_last_error gives the message.  A context is not
+ * thread-safe; distinct contexts are independent.
+ */
+#ifndef PTYCHO_DM_H
+#define PTYCHO_DM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DM_OK 0
+#define DM_EINVAL (-1)      /* bad shape, size, position, pointer or input value */
+#define DM_ENOMEM (-2)      /* an allocation failed */
+#define DM_ECUDA (-3)       /* a CUDA runtime error (text in dm_last_error) */
+#define DM_ENONFINITE (-4)  /* a metric of some iteration was NaN or Inf */
+#define DM_ETIMEOUT (-5)    /* a bounded device-side wait expired */
+
+#define DM_HOST 0
+#define DM_DEVICE 1
+
+/* Steps for dm_run_step (one piece of an iteration, for per-step checks). */
+#define DM_STEP_FOURIER 0   /* Eq. 3 over all views                          */
+#define DM_STEP_OBJECT 1    /* Eq. 5 from the current exit waves and probe   */
+#define DM_STEP_PROBE 2     /* Eq. 4 from the current exit waves and object  */
+
+/* Kernel classes reported by dm_get_timing. */
+#define DM_KERNEL_FOURIER 0       /* persistent Fourier-step kernel (Eq. 3)       */
+#define DM_KERNEL_OBJECT_GATHER 1 /* object numerator/denominator gather (Eq. 5) */
+#define DM_KERNEL_OBJECT_FINAL 2  /* object division and Eq. 6 partials          */
+#define DM_KERNEL_PROBE_PARTIAL 3 /* per-view-group probe sums (Eq. 4)           */
+#define DM_KERNEL_PROBE_FINAL 4   /* probe reduction, division, Eq. 6 partials   */
+#define DM_KERNEL_METRICS 5       /* Eq. 6 / Fourier-error reductions            */
+#define DM_KERNEL_OTHER 6         /* object-source refresh for n_inner > 1, etc. */
+#define DM_KERNEL_COUNT 7
+
+typedef struct dm_ctx dm_ctx;
+
+/* Device allocator hook: return `bytes` of device memory on the context's
+ * device (NULL on failure); free it again.  `user` is alloc_user. */
+typedef void* (*dm_alloc_fn)(size_t bytes, void* user);
+typedef void (*dm_free_fn)(void* ptr, void* user);
+
+typedef struct dm_params {
+  int32_t n;                  /* frame side N: 16, 32, 64, 128 or 256            */
+  int32_t modes;              /* probe modes M, 1..16                            */
+  int32_t views;              /* scan points J >= 1                              */
+  int32_t obj_h, obj_w;       /* object array H x W, each >= N                   */
+  float beta;                 /* Eq. 3 relaxation, in [0, 1]; the paper uses 0.8 */
+  int32_t n_inner;            /* object/probe passes per iteration, >= 1         */
+  int32_t probe_update_start; /* iterations before this index keep P fixed       */
+  double denom_floor_rel;     /* delta = this * max(denominator), >= 0           */
+  int32_t mem_kind;           /* DM_HOST or DM_DEVICE for dm_init's inputs       */
+  dm_alloc_fn alloc;          /* NULL: cudaMallocAsync on the stream             */
+  dm_free_fn free;
+  void* alloc_user;
+  void* stream;               /* cudaStream_t, or NULL for a library stream      */
+  int64_t scratch_bytes;      /* L2-resident Fourier-step scratch; 0 = 64 MiB.   */
+                              /* Smaller values mean smaller view chunks.        */
+} dm_params;
+
+/* Fill p with the defaults: beta 0.8, n_inner 1, probe_update_start 0,
+ * denom_floor_rel 1e-6, mem_kind DM_HOST, no allocator, NULL stream,
+ * default scratch; the sizes are zeroed and must be set by the caller. */
+void dm_params_default(dm_params* p);
+
+/* Create a context on the current CUDA device: validate the parameters,
+ * copy the positions, intensities, probe and object, and build the initial
+ * exit waves psi_j^k = P_k O on every footprint (Sec. II, first step).
+ * Returns DM_EINVAL for a bad size, a footprint outside the object, or an
+ * intensity that is negative or not finite. On failure *out is NULL. */
+int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions,
+            const float* intensities, const float* probe0, const float* object0);
+
+/* Enqueue n_iter >= 0 DM iterations (Eq. 3, then Eq. 5 and Eq. 4 n_inner
+ * times, then Eq. 6).  Asynchronous with respect to the host. */
+int dm_iterate(dm_ctx* ctx, int32_t n_iter);
+
+/* Enqueue one piece of an iteration (DM_STEP_*).  DM_STEP_OBJECT and
+ * DM_STEP_PROBE replace the current object / probe; no metric is written
+ * and the iteration counter does not move. */
+int dm_run_step(dm_ctx* ctx, int32_t step);
+
+/* Copy the current object [H][W][2], probe [M][N][N][2] or exit waves
+ * [J][M][N][N][2] to `out` (host or device by mem_kind); synchronises. */
+int dm_get_object(dm_ctx* ctx, float* out, int32_t mem_kind);
+int dm_get_probe(dm_ctx* ctx, float* out, int32_t mem_kind);
+int dm_get_exit_waves(dm_ctx* ctx, float* out, int32_t mem_kind);
+
+/* Replace the exit waves, object or probe (resume from a checkpoint). */
+int dm_set_exit_waves(dm_ctx* ctx, const float* in, int32_t mem_kind);
+int dm_set_object(dm_ctx* ctx, const float* in, int32_t mem_kind);
+int dm_set_probe(dm_ctx* ctx, const float* in, int32_t mem_kind);
+
+/* Metrics of iteration `iter` (0-based; -1 = the last one).  eps_probe
+ * receives M values.  Any output pointer may be NULL.  Only the last 1024
+ * iterations are kept.  Synchronises; returns DM_ENONFINITE if any metric
+ * computed so far was not finite. */
+int dm_get_error(dm_ctx* ctx, int32_t iter, double* eps_obj, double* eps_probe,
+                 double* fourier_err);
+
+/* Number of completed dm_iterate iterations. */
+int64_t dm_iterations_done(const dm_ctx* ctx);
+
+/* Power sum_u |P_k(u)|^2 of each probe mode (M doubles, host), the quantity
+ * used to choose the number of modes (Sec. II).  Synchronises. */
+int dm_get_mode_power(dm_ctx* ctx, double* out);
+
+/* Wait for all enqueued work; report device-side errors. */
+int dm_sync(dm_ctx* ctx);
+
+/* Per-kernel-class timing with CUDA events on the context's stream.
+ * dm_set_timing(ctx, 1) starts recording (and clears the totals);
+ * dm_get_timing synchronises and returns the accumulated device time and
+ * the number of launches of class `kernel` (DM_KERNEL_*). */
+int dm_set_timing(dm_ctx* ctx, int32_t enable);
+int dm_get_timing(dm_ctx* ctx, int32_t kernel, double* total_ms, int64_t* launches);
+const char* dm_kernel_name(int32_t kernel);
+
+/* Bytes of device memory the context holds. */
+size_t dm_device_bytes(const dm_ctx* ctx);
+
+/* Release everything the context holds (NULL is ignored). */
+void dm_free(dm_ctx* ctx);
+
+/* Message of the last failure on ctx, or of the last failed dm_init when
+ * ctx is NULL.  Valid until the next call on the same context. */
+const char* dm_last_error(const dm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTYCHO_DM_H */

@@ -1,0 +1,751 @@
+// Host side of the C ABI declared in include/dm.h: argument checking, device
+// memory, the launch plans (Fourier task schedule, object-tile CSR lists, TMA
+// tensor map, probe reduction groups) and the order of launches in one
+// difference-map iteration (Sec. II: Eq. 3, then Eq. 5 and Eq. 4, then Eq. 6).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dm.h"
+#include "dm_kernels.h"
+
+namespace {
+
+constexpr size_t kScratchBudget = 64ull << 20;   // L2-resident Fourier scratch
+constexpr size_t kColumnSmemBudget = 72u << 10;  // column strip in shared memory
+constexpr size_t kColumnTaskBytes = 128u << 10;  // scratch bytes per column task
+constexpr int kFourierLag = 1;                   // stages between task kinds
+
+thread_local std::string g_init_error;
+
+struct TimedLaunch {
+  int kind;
+  cudaEvent_t start, stop;
+};
+
+}  // namespace
+
+struct dm_ctx {
+  dm_params p{};
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::vector<std::pair<void*, size_t>> allocs;
+  size_t bytes = 0;
+
+  int N = 0, M = 0, J = 0, H = 0, W = 0;
+
+  float2* psi = nullptr;
+  float2* probe[2] = {nullptr, nullptr};
+  float2* obj[2] = {nullptr, nullptr};
+  float2* cview = nullptr;
+  float2* scratch = nullptr;
+  float2* tw = nullptr;
+  float2* num_O = nullptr;
+  float2* part_num = nullptr;
+  float* istrip = nullptr;
+  float* p2 = nullptr;
+  float* den_O = nullptr;
+  int2* pos = nullptr;
+  int* counters = nullptr;
+  int* stage_off = nullptr;
+  int* status = nullptr;
+  int* tile_ptr = nullptr;
+  int* tile_views = nullptr;
+  unsigned* dmax_O = nullptr;
+  unsigned long long* dmax_P = nullptr;
+  double* ef_part = nullptr;
+  double* isum_part = nullptr;
+  double* isum = nullptr;
+  double* obj_part = nullptr;
+  double* probe_part = nullptr;
+  double* part_den = nullptr;
+  double* num_sum = nullptr;
+  double* den_sum = nullptr;
+  double* ring = nullptr;
+  double* mode_pow = nullptr;
+  int cur_P = 0, cur_O = 0;
+
+  dmk::FourierArgs fa{};
+  int fgrid = 0;
+  size_t fsmem = 0;
+  size_t counters_bytes = 0;
+  int tiles_x = 0, tiles_y = 0, obj_final_blocks = 0;
+  CUtensorMap tmap_c;
+  int probe_groups = 0;
+  int probe_final_blocks = 0;
+  int64_t iters = 0;
+
+  bool timing = false;
+  std::vector<TimedLaunch> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double kms[DM_KERNEL_COUNT] = {};
+  int64_t klaunch[DM_KERNEL_COUNT] = {};
+};
+
+namespace {
+
+int fail(dm_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg; else g_init_error = msg;
+  return code;
+}
+
+int cuda_fail(dm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, DM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define DM_CUDA(ctx, call)                                  \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+int dev_alloc(dm_ctx* c, void** out, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (bytes == 0) bytes = 256;
+  void* ptr = nullptr;
+  if (c->p.alloc) {
+    ptr = c->p.alloc(bytes, c->p.alloc_user);
+  } else if (cudaMallocAsync(&ptr, bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+  }
+  if (!ptr) return fail(c, DM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  c->allocs.emplace_back(ptr, bytes);
+  c->bytes += bytes;
+  *out = ptr;
+  return DM_OK;
+}
+
+template <typename T>
+int alloc_n(dm_ctx* c, T** out, size_t n) {
+  return dev_alloc(c, reinterpret_cast<void**>(out), n * sizeof(T));
+}
+
+void release_all(dm_ctx* c) {
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& a : c->allocs) {
+    if (c->p.alloc && c->p.free) c->p.free(a.first, c->p.alloc_user);
+    else if (!c->p.alloc) cudaFreeAsync(a.first, c->stream);
+  }
+  c->allocs.clear();
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& t : c->pending) { cudaEventDestroy(t.start); cudaEventDestroy(t.stop); }
+  c->pending.clear();
+  for (auto e : c->event_pool) cudaEventDestroy(e);
+  c->event_pool.clear();
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  c->stream = nullptr;
+}
+
+cudaEvent_t take_event(dm_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Bracket one launch with events when timing is on.
+struct Timed {
+  dm_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timed(dm_ctx* ctx, int k) : c(ctx), kind(k) {
+    if (c->timing) {
+      a = take_event(c);
+      b = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~Timed() {
+    if (c->timing && a && b) {
+      cudaEventRecord(b, c->stream);
+      c->pending.push_back({kind, a, b});
+    }
+  }
+};
+
+int collect_timing(dm_ctx* c) {
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (auto& t : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) {
+      c->kms[t.kind] += ms;
+      c->klaunch[t.kind] += 1;
+    }
+    c->event_pool.push_back(t.start);
+    c->event_pool.push_back(t.stop);
+  }
+  c->pending.clear();
+  return DM_OK;
+}
+
+int check_status(dm_ctx* c) {
+  int st = 0;
+  DM_CUDA(c, cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (st & dmk::kStatusTimeout) return fail(c, DM_ETIMEOUT, "a bounded device-side wait expired");
+  if (st & dmk::kStatusNonFinite) return fail(c, DM_ENONFINITE, "a metric was not finite");
+  if (st & dmk::kStatusBadInput) return fail(c, DM_EINVAL, "an intensity was negative or not finite");
+  return DM_OK;
+}
+
+int copy_in(dm_ctx* c, void* dst, const void* src, size_t bytes, int mem_kind) {
+  DM_CUDA(c, cudaMemcpyAsync(dst, src, bytes, mem_kind == DM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                    : cudaMemcpyHostToDevice, c->stream));
+  return DM_OK;
+}
+
+int copy_out(dm_ctx* c, void* dst, const void* src, size_t bytes, int mem_kind) {
+  DM_CUDA(c, cudaMemcpyAsync(dst, src, bytes, mem_kind == DM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                    : cudaMemcpyDeviceToHost, c->stream));
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DM_OK;
+}
+
+bool valid_n(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
+
+// Shared-memory stride of one padded column: N + N/R2 float2 plus a pad that
+// spreads the columns of one warp over distinct banks.
+int column_stride(int N, int R2, int w) {
+  const int base = N + N / R2;
+  int target;
+  if (R2 == 8) target = 8;
+  else if (R2 == 4) target = 4;
+  else target = (w >= 16) ? 1 : (16 / w) % 16;
+  const int pad = ((target - base) % 16 + 16) % 16;
+  return base + pad;
+}
+
+int plan_fourier(dm_ctx* c) {
+  const int N = c->N, M = c->M, J = c->J;
+  const int R2 = dmk::fourier_r2(N);
+  const int groups = dmk::kThreads / R2;
+  const int GR = std::min(groups, N);
+  dmk::FourierArgs& a = c->fa;
+  a.N = N; a.M = M; a.J = J; a.H = c->H; a.W = c->W;
+  a.RB = N / GR;
+  int w = N;
+  while (w > 1 && (size_t)M * w * column_stride(N, R2, w) * sizeof(float2) > kColumnSmemBudget) w >>= 1;
+  a.w = w;
+  a.CS = column_stride(N, R2, w);
+  a.NS = N / w;
+  const size_t strip_bytes = (size_t)M * N * w * sizeof(float2);
+  int spg = 1;
+  while (spg * 2 <= a.NS && strip_bytes * spg * 2 <= kColumnTaskBytes) spg *= 2;
+  a.SPG = spg;
+  a.CG = a.NS / spg;
+  a.lag = kFourierLag;
+  a.nslot = 2 * a.lag + 2;
+  const size_t view_bytes = (size_t)M * N * N * sizeof(float2);
+  const size_t budget = c->p.scratch_bytes > 0 ? (size_t)c->p.scratch_bytes : kScratchBudget;
+  size_t B = budget / ((size_t)a.nslot * view_bytes);
+  B = std::max<size_t>(1, std::min<size_t>(B, (size_t)J));
+  a.B = (int)B;
+  a.nchunks = (J + a.B - 1) / a.B;
+  a.nstages = a.nchunks + 2 * a.lag;
+  std::vector<int> off(a.nstages + 1, 0);
+  auto nv = [&](int ch) { return std::min(a.B, J - ch * a.B); };
+  long long total = 0;
+  for (int s = 0; s < a.nstages; ++s) {
+    off[s] = (int)total;
+    if (s < a.nchunks) total += (long long)nv(s) * a.RB;
+    if (s - a.lag >= 0 && s - a.lag < a.nchunks) total += (long long)nv(s - a.lag) * a.CG;
+    if (s - 2 * a.lag >= 0 && s - 2 * a.lag < a.nchunks) total += (long long)nv(s - 2 * a.lag) * a.RB;
+  }
+  off[a.nstages] = (int)total;
+  if (total >= (1ll << 31)) return fail(c, DM_EINVAL, "too many Fourier tasks");
+  a.total_tasks = (int)total;
+  a.beta = c->p.beta;
+
+  int rc;
+  if ((rc = alloc_n(c, &c->scratch, (size_t)a.nslot * B * M * N * N))) return rc;
+  if ((rc = alloc_n(c, &c->stage_off, off.size()))) return rc;
+  c->counters_bytes = sizeof(int) * (1 + 3 * (size_t)a.nchunks);
+  if ((rc = dev_alloc(c, reinterpret_cast<void**>(&c->counters), c->counters_bytes))) return rc;
+  if ((rc = alloc_n(c, &c->ef_part, (size_t)J * a.CG))) return rc;
+  DM_CUDA(c, cudaMemcpyAsync(c->stage_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             c->stream));
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));  // `off` is a host temporary
+
+  c->fsmem = dmk::fourier_smem_bytes(N, M, w, a.CS);
+  const int occ = dmk::fourier_occupancy(N, c->fsmem);
+  if (occ < 1) return fail(c, DM_ECUDA, "Fourier kernel does not fit on an SM");
+  c->fgrid = std::max(1, std::min(a.total_tasks, occ * c->num_sms));
+
+  a.psi = c->psi; a.istrip = c->istrip; a.pos = c->pos; a.cview = c->cview;
+  a.scratch = c->scratch; a.ef_part = c->ef_part; a.tw = c->tw;
+  a.stage_off = c->stage_off; a.counters = c->counters; a.status = c->status;
+  return DM_OK;
+}
+
+int plan_object(dm_ctx* c, const std::vector<int32_t>& hpos) {
+  const int N = c->N, J = c->J;
+  c->tiles_x = (c->W + dmk::kObjTileW - 1) / dmk::kObjTileW;
+  c->tiles_y = (c->H + dmk::kObjTileH - 1) / dmk::kObjTileH;
+  const int ntiles = c->tiles_x * c->tiles_y;
+  std::vector<int> cnt(ntiles + 1, 0);
+  for (int j = 0; j < J; ++j) {
+    const int r = hpos[2 * j], q = hpos[2 * j + 1];
+    for (int ty = r / dmk::kObjTileH; ty <= (r + N - 1) / dmk::kObjTileH; ++ty)
+      for (int tx = q / dmk::kObjTileW; tx <= (q + N - 1) / dmk::kObjTileW; ++tx) cnt[ty * c->tiles_x + tx + 1]++;
+  }
+  for (int t = 0; t < ntiles; ++t) cnt[t + 1] += cnt[t];
+  std::vector<int> fill(cnt.begin(), cnt.end() - 1), views(cnt[ntiles]);
+  for (int j = 0; j < J; ++j) {
+    const int r = hpos[2 * j], q = hpos[2 * j + 1];
+    for (int ty = r / dmk::kObjTileH; ty <= (r + N - 1) / dmk::kObjTileH; ++ty)
+      for (int tx = q / dmk::kObjTileW; tx <= (q + N - 1) / dmk::kObjTileW; ++tx)
+        views[fill[ty * c->tiles_x + tx]++] = j;
+  }
+  int rc;
+  if ((rc = alloc_n(c, &c->tile_ptr, cnt.size()))) return rc;
+  if ((rc = alloc_n(c, &c->tile_views, std::max<size_t>(1, views.size())))) return rc;
+  DM_CUDA(c, cudaMemcpyAsync(c->tile_ptr, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  if (!views.empty())
+    DM_CUDA(c, cudaMemcpyAsync(c->tile_views, views.data(), views.size() * sizeof(int), cudaMemcpyHostToDevice,
+                               c->stream));
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));
+
+  // TMA view of the object sources: a 2-D array of floats, 2N wide, J*N rows.
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  DM_CUDA(c, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+  if (!fn || q != cudaDriverEntryPointSuccess) return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * N), (cuuint64_t)J * N};
+  const cuuint64_t strides[1] = {(cuuint64_t)(2 * N) * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * dmk::kObjBoxW), (cuuint32_t)dmk::kObjTileH};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(&c->tmap_c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->cview, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  c->obj_final_blocks = 2 * c->num_sms;
+  if ((rc = alloc_n(c, &c->num_O, (size_t)c->H * c->W))) return rc;
+  if ((rc = alloc_n(c, &c->den_O, (size_t)c->H * c->W))) return rc;
+  if ((rc = alloc_n(c, &c->dmax_O, 1))) return rc;
+  if ((rc = alloc_n(c, &c->obj_part, 2 * (size_t)c->obj_final_blocks))) return rc;
+  return DM_OK;
+}
+
+int plan_probe(dm_ctx* c) {
+  const int nn = c->N * c->N;
+  const int utiles = (nn + dmk::kProbePxPerCta - 1) / dmk::kProbePxPerCta;
+  int g = (4 * c->num_sms + utiles - 1) / utiles;
+  g = std::max(1, std::min(g, c->J));
+  c->probe_groups = g;
+  c->probe_final_blocks = std::max(1, std::min((nn + dmk::kThreads - 1) / dmk::kThreads, 256));
+  int rc;
+  if ((rc = alloc_n(c, &c->part_num, (size_t)g * c->M * nn))) return rc;
+  if ((rc = alloc_n(c, &c->part_den, (size_t)g * nn))) return rc;
+  if ((rc = alloc_n(c, &c->num_sum, 2 * (size_t)c->M * nn))) return rc;
+  if ((rc = alloc_n(c, &c->den_sum, (size_t)nn))) return rc;
+  if ((rc = alloc_n(c, &c->dmax_P, 1))) return rc;
+  if ((rc = alloc_n(c, &c->probe_part, (size_t)c->probe_final_blocks * 2 * c->M))) return rc;
+  return DM_OK;
+}
+
+int run_fourier(dm_ctx* c) {
+  DM_CUDA(c, cudaMemsetAsync(c->counters, 0, c->counters_bytes, c->stream));
+  c->fa.probe = c->probe[c->cur_P];
+  c->fa.obj = c->obj[c->cur_O];
+  Timed t(c, DM_KERNEL_FOURIER);
+  DM_CUDA(c, dmk::launch_fourier(c->fa, c->fgrid, c->fsmem, c->stream));
+  return DM_OK;
+}
+
+// Eq. 5 into obj[nxt] from the current object sources; o_start = obj[cur].
+int run_object(dm_ctx* c) {
+  DM_CUDA(c, cudaMemsetAsync(c->dmax_O, 0, sizeof(unsigned), c->stream));
+  dmk::ObjGatherArgs g{};
+  g.N = c->N; g.J = c->J; g.H = c->H; g.W = c->W; g.tiles_x = c->tiles_x;
+  g.pos = c->pos; g.tile_ptr = c->tile_ptr; g.tile_views = c->tile_views; g.p2 = c->p2;
+  g.num = c->num_O; g.den = c->den_O; g.den_max_bits = c->dmax_O; g.status = c->status;
+  {
+    Timed t(c, DM_KERNEL_OBJECT_GATHER);
+    DM_CUDA(c, dmk::launch_obj_gather(&c->tmap_c, g, c->tiles_x * c->tiles_y, c->stream));
+  }
+  dmk::ObjFinalArgs f{};
+  f.H = c->H; f.W = c->W; f.delta_rel = (float)c->p.denom_floor_rel;
+  f.num = c->num_O; f.den = c->den_O; f.den_max_bits = c->dmax_O;
+  f.o_start = c->obj[c->cur_O]; f.o_new = c->obj[c->cur_O ^ 1]; f.part = c->obj_part;
+  Timed t(c, DM_KERNEL_OBJECT_FINAL);
+  DM_CUDA(c, dmk::launch_obj_final(f, c->obj_final_blocks, c->stream));
+  return DM_OK;
+}
+
+// Eq. 4 into probe[nxt] from psi and object `o`; p_start = probe[cur].
+int run_probe(dm_ctx* c, const float2* o) {
+  dmk::ProbePartialArgs a{};
+  a.N = c->N; a.M = c->M; a.J = c->J; a.H = c->H; a.W = c->W; a.groups = c->probe_groups;
+  a.psi = c->psi; a.obj = o; a.pos = c->pos; a.part_num = c->part_num; a.part_den = c->part_den;
+  {
+    Timed t(c, DM_KERNEL_PROBE_PARTIAL);
+    DM_CUDA(c, dmk::launch_probe_partial(a, c->stream));
+  }
+  DM_CUDA(c, cudaMemsetAsync(c->dmax_P, 0, sizeof(unsigned long long), c->stream));
+  dmk::ProbeFinalArgs f{};
+  f.N = c->N; f.M = c->M; f.groups = c->probe_groups; f.delta_rel = (float)c->p.denom_floor_rel;
+  f.part_num = c->part_num; f.part_den = c->part_den; f.p_start = c->probe[c->cur_P];
+  f.p_new = c->probe[c->cur_P ^ 1]; f.p2 = c->p2; f.num_sum = c->num_sum; f.den_sum = c->den_sum;
+  f.den_max_bits = c->dmax_P; f.part = c->probe_part;
+  int blocks = 0;
+  Timed t(c, DM_KERNEL_PROBE_FINAL);
+  DM_CUDA(c, dmk::launch_probe_final(f, c->stream, &blocks));
+  return DM_OK;
+}
+
+int check_ctx(dm_ctx* c) {
+  if (!c) return DM_EINVAL;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  return DM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dm_params_default(dm_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->beta = 0.8f;
+  p->n_inner = 1;
+  p->probe_update_start = 0;
+  p->denom_floor_rel = 1e-6;
+  p->mem_kind = DM_HOST;
+}
+
+int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const float* intensities,
+            const float* probe0, const float* object0) {
+  g_init_error.clear();
+  if (!out) return fail(nullptr, DM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!p) return fail(nullptr, DM_EINVAL, "params is NULL");
+  if (!positions || !intensities || !probe0 || !object0) return fail(nullptr, DM_EINVAL, "an input pointer is NULL");
+  if (!valid_n(p->n)) return fail(nullptr, DM_EINVAL, "n must be 16, 32, 64, 128 or 256");
+  if (p->modes < 1 || p->modes > dmk::kMaxModes) return fail(nullptr, DM_EINVAL, "modes must be in 1..16");
+  if (p->views < 1 || (long long)p->views * p->n >= (1ll << 31))
+    return fail(nullptr, DM_EINVAL, "views out of range");
+  if (p->obj_h < p->n || p->obj_w < p->n || (long long)p->obj_h * p->obj_w >= (1ll << 31))
+    return fail(nullptr, DM_EINVAL, "object must be at least n x n and below 2^31 pixels");
+  if (!(p->beta >= 0.f && p->beta <= 1.f)) return fail(nullptr, DM_EINVAL, "beta must be in [0, 1]");
+  if (p->n_inner < 1) return fail(nullptr, DM_EINVAL, "n_inner must be >= 1");
+  if (p->probe_update_start < 0) return fail(nullptr, DM_EINVAL, "probe_update_start must be >= 0");
+  if (!(p->denom_floor_rel >= 0.0) || !std::isfinite(p->denom_floor_rel))
+    return fail(nullptr, DM_EINVAL, "denom_floor_rel must be finite and >= 0");
+  if (p->mem_kind != DM_HOST && p->mem_kind != DM_DEVICE) return fail(nullptr, DM_EINVAL, "bad mem_kind");
+  if ((p->alloc == nullptr) != (p->free == nullptr)) return fail(nullptr, DM_EINVAL, "alloc and free go together");
+  if (p->scratch_bytes < 0) return fail(nullptr, DM_EINVAL, "scratch_bytes must be >= 0");
+  if (p->mem_kind == DM_HOST) {
+    for (int j = 0; j < p->views; ++j) {
+      const int r = positions[2 * j], q = positions[2 * j + 1];
+      if (r < 0 || q < 0 || r > p->obj_h - p->n || q > p->obj_w - p->n)
+        return fail(nullptr, DM_EINVAL, "footprint of view " + std::to_string(j) + " lies outside the object");
+    }
+  }
+
+  dm_ctx* c = new (std::nothrow) dm_ctx();
+  if (!c) return fail(nullptr, DM_ENOMEM, "out of host memory");
+  c->p = *p;
+  c->N = p->n; c->M = p->modes; c->J = p->views; c->H = p->obj_h; c->W = p->obj_w;
+  auto bail = [&](int rc) {
+    g_init_error = c->err.empty() ? g_init_error : c->err;
+    release_all(c);
+    delete c;
+    return rc;
+  };
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) { cuda_fail(c, e, "cudaGetDevice"); return bail(DM_ECUDA); }
+  e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) { cuda_fail(c, e, "cudaDeviceGetAttribute"); return bail(DM_ECUDA); }
+  if (p->stream) {
+    c->stream = static_cast<cudaStream_t>(p->stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { cuda_fail(c, e, "cudaStreamCreate"); return bail(DM_ECUDA); }
+    c->own_stream = true;
+  }
+
+  const int N = c->N, M = c->M, J = c->J;
+  const size_t nn = (size_t)N * N;
+  // positions: validate on the host (they also drive the object tiling)
+  std::vector<int32_t> hpos(2 * (size_t)J);
+  if (p->mem_kind == DM_DEVICE) {
+    e = cudaMemcpy(hpos.data(), positions, hpos.size() * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { cuda_fail(c, e, "copy positions"); return bail(DM_ECUDA); }
+  } else {
+    std::memcpy(hpos.data(), positions, hpos.size() * sizeof(int32_t));
+  }
+  for (int j = 0; j < J; ++j) {
+    const int r = hpos[2 * j], q = hpos[2 * j + 1];
+    if (r < 0 || q < 0 || r > c->H - N || q > c->W - N) {
+      fail(c, DM_EINVAL, "footprint of view " + std::to_string(j) + " lies outside the object");
+      return bail(DM_EINVAL);
+    }
+  }
+
+  int rc;
+#define DM_TRY(x) do { if ((rc = (x)) != DM_OK) return bail(rc); } while (0)
+  DM_TRY(alloc_n(c, &c->psi, (size_t)J * M * nn));
+  DM_TRY(alloc_n(c, &c->cview, (size_t)J * nn));
+  DM_TRY(alloc_n(c, &c->istrip, (size_t)J * nn));
+  DM_TRY(alloc_n(c, &c->probe[0], (size_t)M * nn));
+  DM_TRY(alloc_n(c, &c->probe[1], (size_t)M * nn));
+  DM_TRY(alloc_n(c, &c->obj[0], (size_t)c->H * c->W));
+  DM_TRY(alloc_n(c, &c->obj[1], (size_t)c->H * c->W));
+  DM_TRY(alloc_n(c, &c->p2, nn));
+  DM_TRY(alloc_n(c, &c->pos, (size_t)J));
+  DM_TRY(alloc_n(c, &c->tw, (size_t)N));
+  DM_TRY(alloc_n(c, &c->status, 1));
+  DM_TRY(alloc_n(c, &c->isum, 1));
+  DM_TRY(alloc_n(c, &c->ring, (size_t)dmk::kMetricsRing * (2 + dmk::kMaxModes)));
+  DM_TRY(alloc_n(c, &c->mode_pow, (size_t)M));
+  if ((e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream)) != cudaSuccess) { cuda_fail(c, e, "memset"); return bail(DM_ECUDA); }
+  if ((e = cudaMemsetAsync(c->ring, 0, sizeof(double) * dmk::kMetricsRing * (2 + dmk::kMaxModes), c->stream)) != cudaSuccess) {
+    cuda_fail(c, e, "memset"); return bail(DM_ECUDA);
+  }
+
+  std::vector<float2> htw(N);
+  for (int m = 0; m < N; ++m) {
+    const double a = -2.0 * M_PI * (double)m / (double)N;
+    htw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  DM_TRY(copy_in(c, c->tw, htw.data(), N * sizeof(float2), DM_HOST));
+  DM_TRY(copy_in(c, c->pos, hpos.data(), hpos.size() * sizeof(int32_t), DM_HOST));
+  DM_TRY(copy_in(c, c->probe[0], probe0, (size_t)M * nn * sizeof(float2), p->mem_kind));
+  DM_TRY(copy_in(c, c->obj[0], object0, (size_t)c->H * c->W * sizeof(float2), p->mem_kind));
+
+  DM_TRY(plan_fourier(c));
+  DM_TRY(plan_object(c, hpos));
+  DM_TRY(plan_probe(c));
+
+  // intensities: strip layout for the column tasks, checked, and sum_q I
+  const float* dev_i = intensities;
+  float* tmp = nullptr;
+  if (p->mem_kind == DM_HOST) {
+    DM_TRY(alloc_n(c, &tmp, (size_t)J * nn));
+    DM_TRY(copy_in(c, tmp, intensities, (size_t)J * nn * sizeof(float), DM_HOST));
+    dev_i = tmp;
+  }
+  double* isum_part = nullptr;
+  DM_TRY(alloc_n(c, &isum_part, 2048));
+  int ib = 0;
+  if ((e = dmk::launch_intensity_layout(c->istrip, dev_i, N, J, c->fa.w, isum_part, c->status, &ib, c->stream)) !=
+      cudaSuccess) { cuda_fail(c, e, "intensity layout"); return bail(DM_ECUDA); }
+  if ((e = dmk::launch_reduce_sum(isum_part, ib, 1, 0, c->isum, c->stream)) != cudaSuccess) {
+    cuda_fail(c, e, "intensity sum"); return bail(DM_ECUDA);
+  }
+  if ((e = dmk::launch_p2(c->p2, c->probe[0], N, M, c->stream)) != cudaSuccess) { cuda_fail(c, e, "p2"); return bail(DM_ECUDA); }
+  if ((e = dmk::launch_init_psi(c->psi, c->probe[0], c->obj[0], c->pos, N, M, J, c->W, c->stream)) != cudaSuccess) {
+    cuda_fail(c, e, "initial exit waves"); return bail(DM_ECUDA);
+  }
+  DM_TRY(check_status(c));
+  // the staging buffers are no longer needed
+  for (void* t : {static_cast<void*>(tmp), static_cast<void*>(isum_part)}) {
+    if (!t) continue;
+    auto it = std::find_if(c->allocs.begin(), c->allocs.end(), [&](const std::pair<void*, size_t>& a) { return a.first == t; });
+    if (it != c->allocs.end()) {
+      if (c->p.alloc) c->p.free(it->first, c->p.alloc_user); else cudaFreeAsync(it->first, c->stream);
+      c->bytes -= it->second;
+      c->allocs.erase(it);
+    }
+  }
+#undef DM_TRY
+  *out = c;
+  return DM_OK;
+}
+
+int dm_iterate(dm_ctx* c, int32_t n_iter) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (n_iter < 0) return fail(c, DM_EINVAL, "n_iter must be >= 0");
+  for (int it = 0; it < n_iter; ++it) {
+    const bool upd = c->iters >= c->p.probe_update_start;
+    if ((rc = run_fourier(c))) return rc;
+    for (int pass = 0; pass < c->p.n_inner; ++pass) {
+      if (pass > 0) {
+        Timed t(c, DM_KERNEL_OTHER);
+        DM_CUDA(c, dmk::launch_obj_source(c->cview, c->psi, c->probe[c->cur_P ^ 1], c->N, c->M, c->J, c->stream));
+      }
+      if ((rc = run_object(c))) return rc;
+      if (!upd) break;  // later passes would repeat the same object update
+      if ((rc = run_probe(c, c->obj[c->cur_O ^ 1]))) return rc;
+    }
+    {
+      Timed t(c, DM_KERNEL_METRICS);
+      DM_CUDA(c, dmk::launch_metrics(c->ef_part, (long long)c->J * c->fa.CG, c->isum, c->obj_part,
+                                     c->obj_final_blocks, c->probe_part, c->probe_final_blocks, c->M, upd ? 1 : 0,
+                                     c->ring, (int)(c->iters % dmk::kMetricsRing), c->status, c->stream));
+    }
+    c->cur_O ^= 1;
+    if (upd) c->cur_P ^= 1;
+    c->iters++;
+  }
+  return DM_OK;
+}
+
+int dm_run_step(dm_ctx* c, int32_t step) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  switch (step) {
+    case DM_STEP_FOURIER:
+      return run_fourier(c);
+    case DM_STEP_OBJECT: {
+      {
+        Timed t(c, DM_KERNEL_OTHER);
+        DM_CUDA(c, dmk::launch_obj_source(c->cview, c->psi, c->probe[c->cur_P], c->N, c->M, c->J, c->stream));
+      }
+      if ((rc = run_object(c))) return rc;
+      c->cur_O ^= 1;
+      return DM_OK;
+    }
+    case DM_STEP_PROBE:
+      if ((rc = run_probe(c, c->obj[c->cur_O]))) return rc;
+      c->cur_P ^= 1;
+      return DM_OK;
+    default:
+      return fail(c, DM_EINVAL, "unknown step");
+  }
+}
+
+int dm_get_object(dm_ctx* c, float* out, int32_t mem_kind) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!out || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad output");
+  if ((rc = copy_out(c, out, c->obj[c->cur_O], (size_t)c->H * c->W * sizeof(float2), mem_kind))) return rc;
+  return check_status(c);
+}
+
+int dm_get_probe(dm_ctx* c, float* out, int32_t mem_kind) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!out || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad output");
+  if ((rc = copy_out(c, out, c->probe[c->cur_P], (size_t)c->M * c->N * c->N * sizeof(float2), mem_kind))) return rc;
+  return check_status(c);
+}
+
+int dm_get_exit_waves(dm_ctx* c, float* out, int32_t mem_kind) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!out || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad output");
+  if ((rc = copy_out(c, out, c->psi, (size_t)c->J * c->M * c->N * c->N * sizeof(float2), mem_kind))) return rc;
+  return check_status(c);
+}
+
+int dm_set_exit_waves(dm_ctx* c, const float* in, int32_t mem_kind) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!in || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad input");
+  if ((rc = copy_in(c, c->psi, in, (size_t)c->J * c->M * c->N * c->N * sizeof(float2), mem_kind))) return rc;
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DM_OK;
+}
+
+int dm_set_object(dm_ctx* c, const float* in, int32_t mem_kind) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!in || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad input");
+  if ((rc = copy_in(c, c->obj[c->cur_O], in, (size_t)c->H * c->W * sizeof(float2), mem_kind))) return rc;
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DM_OK;
+}
+
+int dm_set_probe(dm_ctx* c, const float* in, int32_t mem_kind) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!in || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad input");
+  if ((rc = copy_in(c, c->probe[c->cur_P], in, (size_t)c->M * c->N * c->N * sizeof(float2), mem_kind))) return rc;
+  DM_CUDA(c, dmk::launch_p2(c->p2, c->probe[c->cur_P], c->N, c->M, c->stream));
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DM_OK;
+}
+
+int dm_get_error(dm_ctx* c, int32_t iter, double* eps_obj, double* eps_probe, double* fourier_err) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (c->iters == 0) return fail(c, DM_EINVAL, "no iteration has run");
+  const int64_t it = iter < 0 ? c->iters - 1 : iter;
+  if (it >= c->iters || it < c->iters - dmk::kMetricsRing || it < 0)
+    return fail(c, DM_EINVAL, "iteration not available");
+  double row[2 + dmk::kMaxModes];
+  const size_t bytes = sizeof(double) * (2 + c->M);
+  DM_CUDA(c, cudaMemcpyAsync(row, c->ring + (size_t)(it % dmk::kMetricsRing) * (2 + dmk::kMaxModes), bytes,
+                             cudaMemcpyDeviceToHost, c->stream));
+  if ((rc = check_status(c))) return rc;
+  if (eps_obj) *eps_obj = row[0];
+  if (fourier_err) *fourier_err = row[1];
+  if (eps_probe) for (int k = 0; k < c->M; ++k) eps_probe[k] = row[2 + k];
+  return DM_OK;
+}
+
+int64_t dm_iterations_done(const dm_ctx* c) { return c ? c->iters : -1; }
+
+int dm_get_mode_power(dm_ctx* c, double* out) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!out) return fail(c, DM_EINVAL, "out is NULL");
+  DM_CUDA(c, dmk::launch_mode_power(c->probe[c->cur_P], c->N, c->M, c->mode_pow, c->stream));
+  DM_CUDA(c, cudaMemcpyAsync(out, c->mode_pow, sizeof(double) * c->M, cudaMemcpyDeviceToHost, c->stream));
+  return check_status(c);
+}
+
+int dm_sync(dm_ctx* c) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));
+  DM_CUDA(c, cudaGetLastError());
+  return check_status(c);
+}
+
+int dm_set_timing(dm_ctx* c, int32_t enable) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if ((rc = collect_timing(c))) return rc;
+  for (int k = 0; k < DM_KERNEL_COUNT; ++k) { c->kms[k] = 0.0; c->klaunch[k] = 0; }
+  c->timing = enable != 0;
+  return DM_OK;
+}
+
+int dm_get_timing(dm_ctx* c, int32_t kernel, double* total_ms, int64_t* launches) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (kernel < 0 || kernel >= DM_KERNEL_COUNT) return fail(c, DM_EINVAL, "unknown kernel class");
+  if ((rc = collect_timing(c))) return rc;
+  if (total_ms) *total_ms = c->kms[kernel];
+  if (launches) *launches = c->klaunch[kernel];
+  return DM_OK;
+}
+
+const char* dm_kernel_name(int32_t kernel) {
+  static const char* names[DM_KERNEL_COUNT] = {"fourier",       "object_gather", "object_final", "probe_partial",
+                                               "probe_final",   "metrics",       "other"};
+  return (kernel >= 0 && kernel < DM_KERNEL_COUNT) ? names[kernel] : "unknown";
+}
+
+size_t dm_device_bytes(const dm_ctx* c) { return c ? c->bytes : 0; }
+
+void dm_free(dm_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  release_all(c);
+  delete c;
+}
+
+const char* dm_last_error(const dm_ctx* c) { return c ? c->err.c_str() : g_init_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Internal interface between the host orchestrator (dm_api.cu) and the
+// kernels (dm_fourier.cu, dm_overlap.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dmk {
+
+// Status bits the kernels OR into a device word; the host maps them to
+// DM_E* codes at the next synchronising call.
+enum : int {
+  kStatusTimeout = 1,     // a bounded spin-wait expired
+  kStatusNonFinite = 2,   // a metric was NaN or Inf
+  kStatusBadInput = 4,    // an intensity was negative or not finite
+};
+
+constexpr int kThreads = 256;          // threads per CTA of every hot kernel
+constexpr int kMetricsRing = 1024;     // iterations of metrics kept on the device
+constexpr int kMaxModes = 16;
+
+// ---------------------------------------------------------------------------
+// Fourier step (Eq. 3): one persistent launch over all views.
+// Views are processed in chunks of B; each chunk goes through three task
+// kinds that exchange data through an L2-resident scratch slot:
+//   R: rows of (2 P O - psi) -> forward row DFT           -> slot  (T)
+//   C: column strip, all modes -> forward column DFT, modulus projection,
+//      inverse column DFT, U = beta T'' - T / N            -> slot  (U)
+//   I: inverse row DFT of U, psi' = (2 - beta) P O + G[U], object source
+//      c_j = sum_k conj(P_k) psi'_k                         -> psi, cview
+// Task order is software-pipelined: stage s holds R(s), C(s - lag),
+// I(s - 2 lag); a task waits (bounded) on counters of the chunk it depends on.
+// ---------------------------------------------------------------------------
+struct FourierArgs {
+  int N, M, J, H, W;
+  float beta;
+  float2* psi;            // [J][M][N][N]
+  const float* istrip;    // intensities in strip layout [J][NS][w][N]
+  const float2* probe;    // [M][N][N]
+  const float2* obj;      // [H][W]
+  const int2* pos;        // [J] (row, col)
+  float2* cview;          // [J][N][N] object source sum_k conj(P_k) psi_k
+  float2* scratch;        // [nslot][B][M][N][N]
+  double* ef_part;        // [J][CG] Fourier-error numerator partials
+  const float2* tw;       // [N] exp(-2 pi i m / N)
+  int B, nchunks, lag, nslot;
+  int RB;                 // row tasks per view (row blocks)
+  int CG;                 // column tasks per view (strip groups)
+  int SPG;                // strips per column task
+  int w;                  // strip width (columns)
+  int NS;                 // strips per view = N / w
+  int CS;                 // shared-memory stride of one column (float2)
+  int nstages, total_tasks;
+  const int* stage_off;   // [nstages + 1] first task of each stage
+  int* counters;          // [0] dispenser, then done R/C/I per chunk
+  int* status;
+};
+
+// ---------------------------------------------------------------------------
+// Object update (Eq. 5): gather over the views that cover each object tile.
+// ---------------------------------------------------------------------------
+constexpr int kObjTileH = 32, kObjTileW = 32;
+constexpr int kObjBoxW = kObjTileW + 2;     // complex columns per TMA box
+constexpr int kObjStages = 4;
+
+struct ObjGatherArgs {
+  int N, J, H, W, tiles_x;
+  const int2* pos;
+  const int* tile_ptr;     // [ntiles + 1]
+  const int* tile_views;   // CSR lists (ascending view index)
+  const float* p2;         // [N][N] sum_k |P_k|^2
+  float2* num;             // [H][W]
+  float* den;              // [H][W]
+  unsigned* den_max_bits;  // max over the object (float bits, den >= 0)
+  int* status;
+};
+
+struct ObjFinalArgs {
+  int H, W;
+  float delta_rel;
+  const float2* num;
+  const float* den;
+  const unsigned* den_max_bits;
+  const float2* o_start;   // object at the start of the iteration
+  float2* o_new;
+  double* part;            // [blocks][2]: sum |O_new - O_start|^2, sum |O_new|^2
+};
+
+// ---------------------------------------------------------------------------
+// Probe update (Eq. 4): per-view-group partial sums, then a fixed-order
+// FP64 reduction over the groups and the division.
+// ---------------------------------------------------------------------------
+constexpr int kProbePxPerThread = 2;
+constexpr int kProbePxPerCta = kThreads * kProbePxPerThread;
+
+struct ProbePartialArgs {
+  int N, M, J, H, W, groups;
+  const float2* psi;
+  const float2* obj;
+  const int2* pos;
+  float2* part_num;        // [groups][M][N*N]
+  double* part_den;        // [groups][N*N]
+};
+
+struct ProbeFinalArgs {
+  int N, M, groups;
+  float delta_rel;
+  const float2* part_num;
+  const double* part_den;
+  const float2* p_start;   // probe at the start of the iteration
+  float2* p_new;
+  float* p2;               // [N*N] sum_k |P_k|^2 of the new probe
+  double* num_sum;         // [M][N*N][2] scratch for the FP64 sums
+  double* den_sum;         // [N*N]
+  unsigned long long* den_max_bits;
+  double* part;            // [blocks][1 + 2M] partial Eq. 6 sums
+};
+
+// Launchers (return the launch error).
+cudaError_t launch_fourier(const FourierArgs& a, int grid, size_t smem, cudaStream_t s);
+size_t fourier_smem_bytes(int N, int M, int w, int CS);
+int fourier_occupancy(int N, size_t smem);
+int fourier_r2(int N);
+
+cudaError_t launch_obj_gather(const void* tmap, const ObjGatherArgs& a, int ntiles, cudaStream_t s);
+cudaError_t launch_obj_final(const ObjFinalArgs& a, int blocks, cudaStream_t s);
+cudaError_t launch_obj_source(float2* cview, const float2* psi, const float2* probe, int N, int M,
+                              int J, cudaStream_t s);
+cudaError_t launch_probe_partial(const ProbePartialArgs& a, cudaStream_t s);
+cudaError_t launch_probe_final(const ProbeFinalArgs& a, cudaStream_t s, int* blocks_out);
+
+cudaError_t launch_init_psi(float2* psi, const float2* probe, const float2* obj, const int2* pos,
+                            int N, int M, int J, int W, cudaStream_t s);
+cudaError_t launch_intensity_layout(float* istrip, const float* inten, int N, int J, int w,
+                                    double* isum_part, int* status, int* blocks_out, cudaStream_t s);
+cudaError_t launch_p2(float* p2, const float2* probe, int N, int M, cudaStream_t s);
+cudaError_t launch_reduce_sum(const double* in, long long n, int stride, int offset, double* out,
+                              cudaStream_t s);
+cudaError_t launch_metrics(const double* ef_part, long long n_ef, const double* isum,
+                           const double* obj_part, int n_obj, const double* probe_part,
+                           int n_probe, int M, int probe_updated, double* ring, int slot,
+                           int* status, cudaStream_t s);
+cudaError_t launch_mode_power(const float2* probe, int N, int M, double* out, cudaStream_t s);
+
+}  // namespace dmk

@@ -1,0 +1,503 @@
+// Overlap projection of the difference map: the object update (Eq. 5) as a
+// gather over the views that cover each object tile, staged through TMA, and
+// the probe update (Eq. 4) as a two-stage deterministic reduction over views.
+// Also the small kernels around them: initial exit waves (Sec. II), the
+// intensity layout, sum_k |P_k|^2, and the Eq. 6 / Fourier-error reductions.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "dm_fft.cuh"
+#include "dm_kernels.h"
+#include "dm_ptx.cuh"
+
+namespace dmk {
+
+// Fixed-order block sum of a double; every thread gets the result.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+  return t;
+}
+
+__device__ __forceinline__ float block_max(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmaxf(t, sh[i]);
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Object update, part 1 (Eq. 5 numerator and denominator).
+// One CTA per 32x32 object tile walks the tile's list of covering views in
+// ascending order.  For each view, TMA brings the 32 x 34 box of the view's
+// object source c_j(u) = sum_k conj(P_k(u)) psi_j^k(u) around the tile into a
+// 4-stage shared-memory ring; each thread accumulates 4 pixels:
+//   num(r) += c_j(r - r_j),   den(r) += sum_k |P_k(r - r_j)|^2.
+// Denominators are summed in FP32 over blocks of 32 views and in FP64 across
+// blocks.  The object is never the target of an atomic; only the global max
+// of den uses one (order-independent, so the result is deterministic).
+// ---------------------------------------------------------------------------
+constexpr int kObjBoxF2 = kObjBoxW * kObjTileH;  // float2 per stage
+
+__global__ void __launch_bounds__(kThreads) k_obj_gather(const __grid_constant__ CUtensorMap tmap,
+                                                         const ObjGatherArgs a) {
+  __shared__ __align__(128) float2 box[kObjStages][kObjBoxF2];
+  __shared__ __align__(8) uint64_t full[kObjStages];
+  __shared__ float shm[kThreads / 32];
+  __shared__ int s_abort;
+  const int tile = blockIdx.x;
+  const int ty0 = (tile / a.tiles_x) * kObjTileH, tx0 = (tile % a.tiles_x) * kObjTileW;
+  const int v0 = a.tile_ptr[tile], nv = a.tile_ptr[tile + 1] - v0;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int N = a.N;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kObjStages; ++s) mbar_init(&full[s], 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+
+  auto issue = [&](int i) {
+    const int j = __ldg(a.tile_views + v0 + i);
+    const int2 p = __ldg(a.pos + j);
+    const int x0e = (tx0 - p.y) & ~1;  // even complex column: 16-byte aligned TMA x
+    const int s = i % kObjStages;
+    mbar_arrive_expect_tx(&full[s], kObjBoxF2 * (uint32_t)sizeof(float2));
+    tma_load_2d(&box[s][0], &tmap, 2 * x0e, j * N + (ty0 - p.x), &full[s]);
+  };
+  int issued = 0;
+  if (threadIdx.x == 0) {
+    for (; issued < nv && issued < kObjStages; ++issued) issue(issued);
+  }
+
+  float2 num[4];
+  float den32[4];
+  double den64[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) { num[m] = make_float2(0.f, 0.f); den32[m] = 0.f; den64[m] = 0.0; }
+
+  int consumed = 0;
+  for (int i = 0; i < nv; ++i) {
+    const int s = i % kObjStages;
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&full[s], (uint32_t)((i / kObjStages) & 1), a.status))
+      s_abort = 1;
+    __syncthreads();
+    if (s_abort) break;
+    const int j = __ldg(a.tile_views + v0 + i);
+    const int2 p = __ldg(a.pos + j);
+    const int x0e = (tx0 - p.y) & ~1;
+    const int ux = tx0 + tx - p.y;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int uy = ty0 + ty + 8 * m - p.x;
+      if (uy >= 0 && uy < N && ux >= 0 && ux < N) {
+        num[m] = cadd(num[m], box[s][(ty + 8 * m) * kObjBoxW + (ux - x0e)]);
+        den32[m] += __ldg(a.p2 + uy * N + ux);
+      }
+    }
+    if ((i & 31) == 31) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) { den64[m] += den32[m]; den32[m] = 0.f; }
+    }
+    consumed = i + 1;
+    __syncthreads();
+    if (threadIdx.x == 0 && issued < nv) { issue(issued); ++issued; }
+  }
+  if (s_abort) {
+    // Let every copy still in flight land before the CTA exits (bounded).
+    if (threadIdx.x == 0) {
+      for (int i = consumed; i < issued; ++i)
+        mbar_wait_bounded(&full[i % kObjStages], (uint32_t)((i / kObjStages) & 1), a.status);
+    }
+    __syncthreads();
+  }
+  float lmax = 0.f;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    den64[m] += den32[m];
+    const int r = ty0 + ty + 8 * m, c = tx0 + tx;
+    if (r < a.H && c < a.W) {
+      const float d = (float)den64[m];
+      a.num[(size_t)r * a.W + c] = num[m];
+      a.den[(size_t)r * a.W + c] = d;
+      lmax = fmaxf(lmax, d);
+    }
+  }
+  const float bm = block_max(lmax, shm);
+  if (threadIdx.x == 0 && bm > 0.f) atomicMax(a.den_max_bits, __float_as_uint(bm));
+}
+
+// Object update, part 2: O = num / (den + delta) on covered pixels, the
+// starting value elsewhere; Eq. 6 partial sums against the starting object.
+__global__ void __launch_bounds__(kThreads) k_obj_final(const ObjFinalArgs a) {
+  __shared__ double sh[kThreads / 32];
+  const float delta = a.delta_rel * __uint_as_float(*a.den_max_bits);
+  const size_t n = (size_t)a.H * a.W;
+  double d2 = 0.0, n2 = 0.0;
+  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kThreads) {
+    const float den = a.den[i];
+    const float2 o0 = a.o_start[i];
+    float2 on = o0;
+    if (den > 0.f) {
+      const float2 nm = a.num[i];
+      const float dd = den + delta;
+      on = make_float2(nm.x / dd, nm.y / dd);
+    }
+    a.o_new[i] = on;
+    const float2 df = csub(on, o0);
+    d2 += (double)df.x * df.x + (double)df.y * df.y;
+    n2 += (double)on.x * on.x + (double)on.y * on.y;
+  }
+  d2 = block_sum(d2, sh);
+  n2 = block_sum(n2, sh);
+  if (threadIdx.x == 0) {
+    a.part[2 * blockIdx.x] = d2;
+    a.part[2 * blockIdx.x + 1] = n2;
+  }
+}
+
+// c_j(u) = sum_k conj(P_k(u)) psi_j^k(u): the object source, recomputed from
+// the exit waves when an inner overlap pass has changed the probe.
+__global__ void __launch_bounds__(kThreads) k_obj_source(float2* cview, const float2* psi,
+                                                         const float2* probe, int N, int M, int J) {
+  const size_t nn = (size_t)N * N;
+  const size_t tot = (size_t)J * nn;
+  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < tot; i += (size_t)gridDim.x * kThreads) {
+    const size_t j = i / nn, u = i % nn;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = 0; k < M; ++k) acc = cadd(acc, cconjmul(__ldg(probe + k * nn + u), __ldcs(psi + (j * M + k) * nn + u)));
+    cview[i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Probe update, part 1 (Eq. 4): CTA (pixel tile, view group) sums over its
+// views, for 2 pixels per thread and all modes:
+//   num_k(u) += conj(O(r_j + u)) psi_j^k(u),   den(u) += |O(r_j + u)|^2
+// (num in FP32, den in FP32 over 32 views then FP64), and writes partials.
+// ---------------------------------------------------------------------------
+template <int MAXM>
+__global__ void __launch_bounds__(kThreads) k_probe_partial(const ProbePartialArgs a) {
+  const int N = a.N, M = a.M;
+  const int nn = N * N;
+  const int g = blockIdx.y;
+  const int j0 = (int)(((long long)g * a.J) / a.groups);
+  const int j1 = (int)(((long long)(g + 1) * a.J) / a.groups);
+  int u[kProbePxPerThread], uy[kProbePxPerThread], ux[kProbePxPerThread];
+  bool ok[kProbePxPerThread];
+  float2 acc[kProbePxPerThread][MAXM];
+  float den32[kProbePxPerThread];
+  double den64[kProbePxPerThread];
+#pragma unroll
+  for (int q = 0; q < kProbePxPerThread; ++q) {
+    u[q] = blockIdx.x * kProbePxPerCta + q * kThreads + threadIdx.x;
+    ok[q] = u[q] < nn;
+    uy[q] = u[q] / N;
+    ux[q] = u[q] % N;
+    den32[q] = 0.f;
+    den64[q] = 0.0;
+#pragma unroll
+    for (int k = 0; k < MAXM; ++k) acc[q][k] = make_float2(0.f, 0.f);
+  }
+  for (int j = j0; j < j1; ++j) {
+    const int2 p = __ldg(a.pos + j);
+#pragma unroll
+    for (int q = 0; q < kProbePxPerThread; ++q) {
+      if (!ok[q]) continue;
+      const float2 o = __ldg(a.obj + (size_t)(p.x + uy[q]) * a.W + p.y + ux[q]);
+      den32[q] = fmaf(o.x, o.x, fmaf(o.y, o.y, den32[q]));
+      const float2* ps = a.psi + (size_t)j * M * nn + u[q];
+#pragma unroll
+      for (int k = 0; k < MAXM; ++k)
+        if (k < M) acc[q][k] = cadd(acc[q][k], cconjmul(o, __ldcs(ps + (size_t)k * nn)));
+    }
+    if (((j - j0) & 31) == 31) {
+#pragma unroll
+      for (int q = 0; q < kProbePxPerThread; ++q) { den64[q] += den32[q]; den32[q] = 0.f; }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kProbePxPerThread; ++q) {
+    if (!ok[q]) continue;
+    a.part_den[(size_t)g * nn + u[q]] = den64[q] + den32[q];
+#pragma unroll
+    for (int k = 0; k < MAXM; ++k)
+      if (k < M) a.part_num[((size_t)g * M + k) * nn + u[q]] = acc[q][k];
+  }
+}
+
+// Probe update, part 2a: FP64 sums over the view groups, in group order.
+__global__ void __launch_bounds__(kThreads) k_probe_sum(const ProbeFinalArgs a) {
+  __shared__ float shm[kThreads / 32];
+  const int nn = a.N * a.N;
+  const size_t tot = (size_t)(a.M + 1) * nn;
+  double lmax = 0.0;
+  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < tot; i += (size_t)gridDim.x * kThreads) {
+    if (i < (size_t)a.M * nn) {
+      double re = 0.0, im = 0.0;
+      for (int g = 0; g < a.groups; ++g) {
+        const float2 v = a.part_num[(size_t)g * a.M * nn + i];
+        re += v.x;
+        im += v.y;
+      }
+      a.num_sum[2 * i] = re;
+      a.num_sum[2 * i + 1] = im;
+    } else {
+      const size_t u = i - (size_t)a.M * nn;
+      double d = 0.0;
+      for (int g = 0; g < a.groups; ++g) d += a.part_den[(size_t)g * nn + u];
+      a.den_sum[u] = d;
+      lmax = fmax(lmax, d);
+    }
+  }
+  // the max is only used through delta = delta_rel * max: a float max is ample
+  const float bm = block_max((float)lmax, shm);
+  if (threadIdx.x == 0 && bm > 0.f) atomicMax(a.den_max_bits, (unsigned long long)__double_as_longlong((double)bm));
+}
+
+// Probe update, part 2b: division, sum_k |P_k|^2 and Eq. 6 partials per mode.
+__global__ void __launch_bounds__(kThreads) k_probe_div(const ProbeFinalArgs a) {
+  __shared__ double sh[kThreads / 32];
+  const int nn = a.N * a.N;
+  const double delta = (double)a.delta_rel * __longlong_as_double((long long)*a.den_max_bits);
+  double d2[kMaxModes], n2[kMaxModes];
+#pragma unroll
+  for (int k = 0; k < kMaxModes; ++k) { d2[k] = 0.0; n2[k] = 0.0; }
+  for (int u = blockIdx.x * kThreads + threadIdx.x; u < nn; u += gridDim.x * kThreads) {
+    const double den = a.den_sum[u];
+    float p2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMaxModes; ++k) {
+      if (k >= a.M) break;
+      const size_t i = (size_t)k * nn + u;
+      const float2 p0 = a.p_start[i];
+      float2 pn = p0;
+      if (den > 0.0) {
+        const double dd = den + delta;
+        pn = make_float2((float)(a.num_sum[2 * i] / dd), (float)(a.num_sum[2 * i + 1] / dd));
+      }
+      a.p_new[i] = pn;
+      const float2 df = csub(pn, p0);
+      d2[k] += (double)df.x * df.x + (double)df.y * df.y;
+      n2[k] += (double)pn.x * pn.x + (double)pn.y * pn.y;
+      p2 += cnorm(pn);
+    }
+    a.p2[u] = p2;
+  }
+  const int stride = 2 * a.M;
+  for (int k = 0; k < a.M; ++k) {
+    const double s1 = block_sum(d2[k], sh);
+    const double s2 = block_sum(n2[k], sh);
+    if (threadIdx.x == 0) {
+      a.part[(size_t)blockIdx.x * stride + 2 * k] = s1;
+      a.part[(size_t)blockIdx.x * stride + 2 * k + 1] = s2;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small kernels.
+// ---------------------------------------------------------------------------
+// psi_j^k(u) = P_k(u) O(r_j + u): the initial fields (Sec. II, first step).
+__global__ void __launch_bounds__(kThreads) k_init_psi(float2* psi, const float2* probe, const float2* obj,
+                                                       const int2* pos, int N, int M, int J, int W) {
+  const size_t nn = (size_t)N * N;
+  const size_t tot = (size_t)J * M * nn;
+  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < tot; i += (size_t)gridDim.x * kThreads) {
+    const size_t u = i % nn;
+    const size_t jk = i / nn;
+    const int k = (int)(jk % M), j = (int)(jk / M);
+    const int y = (int)(u / N), x = (int)(u % N);
+    const int2 p = pos[j];
+    psi[i] = cmul(probe[k * nn + u], obj[(size_t)(p.x + y) * W + p.y + x]);
+  }
+}
+
+// I[j][y][x] -> strip layout [j][s][c][y] with x = s*w + c; flags negative or
+// non-finite values; per-block FP64 partial sums of I.
+__global__ void __launch_bounds__(kThreads) k_intensity_layout(float* istrip, const float* inten, int N, int J,
+                                                               int w, double* part, int* status) {
+  __shared__ double sh[kThreads / 32];
+  const size_t nn = (size_t)N * N;
+  const size_t tot = (size_t)J * nn;
+  double acc = 0.0;
+  bool bad = false;
+  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < tot; i += (size_t)gridDim.x * kThreads) {
+    const size_t j = i / nn, r = i % nn;
+    const int y = (int)(r / N), x = (int)(r % N);
+    const float v = inten[i];
+    if (!(v >= 0.f) || isinf(v)) bad = true;
+    const int s = x / w, c = x % w;
+    istrip[j * nn + ((size_t)s * w + c) * N + y] = v;
+    acc += (double)v;
+  }
+  if (bad) atomicOr(status, kStatusBadInput);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kThreads) k_p2(float* p2, const float2* probe, int N, int M) {
+  const int nn = N * N;
+  for (int u = blockIdx.x * kThreads + threadIdx.x; u < nn; u += gridDim.x * kThreads) {
+    float s = 0.f;
+    for (int k = 0; k < M; ++k) s += cnorm(probe[(size_t)k * nn + u]);
+    p2[u] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mode_power(const float2* probe, int N, double* out) {
+  __shared__ double sh[kThreads / 32];
+  const int nn = N * N;
+  const float2* pk = probe + (size_t)blockIdx.x * nn;
+  double s = 0.0;
+  for (int u = threadIdx.x; u < nn; u += kThreads) s += (double)cnorm(pk[u]);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// out = sum_i in[i * stride + offset], i < n, in a fixed order (one CTA).
+__global__ void __launch_bounds__(kThreads) k_reduce_sum(const double* in, long long n, int stride, int offset,
+                                                         double* out) {
+  __shared__ double sh[kThreads / 32];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += kThreads) s += in[i * stride + offset];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// Eq. 6 for the object and each probe mode, and the Fourier error, into the
+// metrics ring (row = [eps_obj, fourier_err, eps_probe[0..M-1]]).
+__global__ void __launch_bounds__(kThreads) k_metrics(const double* ef_part, long long n_ef, const double* isum,
+                                                      const double* obj_part, int n_obj,
+                                                      const double* probe_part, int n_probe, int M,
+                                                      int probe_updated, double* ring, int slot, int* status) {
+  __shared__ double sh[kThreads / 32];
+  double ef = 0.0;
+  for (long long i = threadIdx.x; i < n_ef; i += kThreads) ef += ef_part[i];
+  ef = block_sum(ef, sh);
+  double od = 0.0, on = 0.0;
+  for (int i = threadIdx.x; i < n_obj; i += kThreads) { od += obj_part[2 * i]; on += obj_part[2 * i + 1]; }
+  od = block_sum(od, sh);
+  on = block_sum(on, sh);
+  double* row = ring + (size_t)slot * (2 + kMaxModes);
+  bool bad = false;
+  if (threadIdx.x == 0) {
+    const double is = *isum;
+    row[0] = on > 0.0 ? sqrt(od / on) : 0.0;
+    row[1] = is > 0.0 ? sqrt(ef / is) : 0.0;
+    bad = !isfinite(row[0]) || !isfinite(row[1]);
+  }
+  for (int k = 0; k < M; ++k) {
+    double pd = 0.0, pn = 0.0;
+    if (probe_updated) {
+      for (int i = threadIdx.x; i < n_probe; i += kThreads) {
+        pd += probe_part[(size_t)i * 2 * M + 2 * k];
+        pn += probe_part[(size_t)i * 2 * M + 2 * k + 1];
+      }
+    }
+    pd = block_sum(pd, sh);
+    pn = block_sum(pn, sh);
+    if (threadIdx.x == 0) {
+      row[2 + k] = pn > 0.0 ? sqrt(pd / pn) : 0.0;
+      bad = bad || !isfinite(row[2 + k]);
+    }
+  }
+  if (threadIdx.x == 0 && bad) atomicOr(status, kStatusNonFinite);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+static int grid_for(size_t work, int cap) {
+  size_t g = (work + kThreads - 1) / kThreads;
+  if (g < 1) g = 1;
+  return (int)(g < (size_t)cap ? g : (size_t)cap);
+}
+
+cudaError_t launch_obj_gather(const void* tmap, const ObjGatherArgs& a, int ntiles, cudaStream_t s) {
+  k_obj_gather<<<ntiles, kThreads, 0, s>>>(*static_cast<const CUtensorMap*>(tmap), a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_obj_final(const ObjFinalArgs& a, int blocks, cudaStream_t s) {
+  k_obj_final<<<blocks, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_obj_source(float2* cview, const float2* psi, const float2* probe, int N, int M, int J,
+                              cudaStream_t s) {
+  k_obj_source<<<grid_for((size_t)J * N * N, 4096), kThreads, 0, s>>>(cview, psi, probe, N, M, J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_partial(const ProbePartialArgs& a, cudaStream_t s) {
+  const int nn = a.N * a.N;
+  dim3 grid((nn + kProbePxPerCta - 1) / kProbePxPerCta, a.groups);
+  if (a.M <= 1) k_probe_partial<1><<<grid, kThreads, 0, s>>>(a);
+  else if (a.M <= 2) k_probe_partial<2><<<grid, kThreads, 0, s>>>(a);
+  else if (a.M <= 4) k_probe_partial<4><<<grid, kThreads, 0, s>>>(a);
+  else if (a.M <= 8) k_probe_partial<8><<<grid, kThreads, 0, s>>>(a);
+  else k_probe_partial<16><<<grid, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Runs 2a and 2b; *blocks_out receives the number of partial rows of 2b.
+cudaError_t launch_probe_final(const ProbeFinalArgs& a, cudaStream_t s, int* blocks_out) {
+  const int nn = a.N * a.N;
+  k_probe_sum<<<grid_for((size_t)(a.M + 1) * nn, 1024), kThreads, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int b = grid_for((size_t)nn, 256);
+  k_probe_div<<<b, kThreads, 0, s>>>(a);
+  *blocks_out = b;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_psi(float2* psi, const float2* probe, const float2* obj, const int2* pos, int N, int M,
+                            int J, int W, cudaStream_t s) {
+  k_init_psi<<<grid_for((size_t)J * M * N * N, 8192), kThreads, 0, s>>>(psi, probe, obj, pos, N, M, J, W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_intensity_layout(float* istrip, const float* inten, int N, int J, int w, double* isum_part,
+                                    int* status, int* blocks_out, cudaStream_t s) {
+  const int b = grid_for((size_t)J * N * N, 2048);
+  k_intensity_layout<<<b, kThreads, 0, s>>>(istrip, inten, N, J, w, isum_part, status);
+  *blocks_out = b;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_p2(float* p2, const float2* probe, int N, int M, cudaStream_t s) {
+  k_p2<<<grid_for((size_t)N * N, 256), kThreads, 0, s>>>(p2, probe, N, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_sum(const double* in, long long n, int stride, int offset, double* out, cudaStream_t s) {
+  k_reduce_sum<<<1, kThreads, 0, s>>>(in, n, stride, offset, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_metrics(const double* ef_part, long long n_ef, const double* isum, const double* obj_part,
+                           int n_obj, const double* probe_part, int n_probe, int M, int probe_updated,
+                           double* ring, int slot, int* status, cudaStream_t s) {
+  k_metrics<<<1, kThreads, 0, s>>>(ef_part, n_ef, isum, obj_part, n_obj, probe_part, n_probe, M, probe_updated,
+                                   ring, slot, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mode_power(const float2* probe, int N, int M, double* out, cudaStream_t s) {
+  k_mode_power<<<M, kThreads, 0, s>>>(probe, N, out);
+  return cudaGetLastError();
+}
+
+}  // namespace dmk

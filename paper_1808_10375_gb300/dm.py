@@ -1,0 +1,332 @@
+"""ctypes binding of the C ABI in include/dm.h (argument marshalling only).
+
+Every function keeps the C name.  Arrays may be NumPy arrays (host memory) or
+torch tensors (host or CUDA); complex arrays are complex64, intensities
+float32, positions int32.  Device memory for a context comes from torch's
+caching allocator when torch has CUDA (passed through the ``alloc``/``free``
+hooks of ``dm_params``), and all work runs on the stream given at dm_init
+(torch's current stream by default).
+
+Loading fails loudly when the compiled library is missing: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libptycho_dm.so")
+
+DM_OK, DM_EINVAL, DM_ENOMEM, DM_ECUDA, DM_ENONFINITE, DM_ETIMEOUT = 0, -1, -2, -3, -4, -5
+DM_HOST, DM_DEVICE = 0, 1
+DM_STEP_FOURIER, DM_STEP_OBJECT, DM_STEP_PROBE = 0, 1, 2
+(DM_KERNEL_FOURIER, DM_KERNEL_OBJECT_GATHER, DM_KERNEL_OBJECT_FINAL, DM_KERNEL_PROBE_PARTIAL,
+ DM_KERNEL_PROBE_FINAL, DM_KERNEL_METRICS, DM_KERNEL_OTHER, DM_KERNEL_COUNT) = range(8)
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class dm_params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("modes", ctypes.c_int32), ("views", ctypes.c_int32),
+        ("obj_h", ctypes.c_int32), ("obj_w", ctypes.c_int32),
+        ("beta", ctypes.c_float), ("n_inner", ctypes.c_int32),
+        ("probe_update_start", ctypes.c_int32), ("denom_floor_rel", ctypes.c_double),
+        ("mem_kind", ctypes.c_int32),
+        ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+        ("stream", ctypes.c_void_p),
+        ("scratch_bytes", ctypes.c_int64),
+    ]
+
+
+class DMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"DM error {code}: {msg}")
+        self.code = code
+
+
+EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_object", "dm_get_probe",
+           "dm_get_exit_waves", "dm_set_exit_waves", "dm_set_object", "dm_set_probe", "dm_get_error",
+           "dm_iterations_done", "dm_get_mode_power", "dm_sync", "dm_set_timing", "dm_get_timing",
+           "dm_kernel_name", "dm_device_bytes", "dm_free", "dm_last_error"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1808_10375_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, i32, i64, f32p, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, P(ctypes.c_float), P(ctypes.c_double)
+    sig = {
+        "dm_params_default": (None, [P(dm_params)]),
+        "dm_init": (ctypes.c_int, [P(vp), P(dm_params), vp, vp, vp, vp]),
+        "dm_iterate": (ctypes.c_int, [vp, i32]),
+        "dm_run_step": (ctypes.c_int, [vp, i32]),
+        "dm_get_object": (ctypes.c_int, [vp, vp, i32]),
+        "dm_get_probe": (ctypes.c_int, [vp, vp, i32]),
+        "dm_get_exit_waves": (ctypes.c_int, [vp, vp, i32]),
+        "dm_set_exit_waves": (ctypes.c_int, [vp, vp, i32]),
+        "dm_set_object": (ctypes.c_int, [vp, vp, i32]),
+        "dm_set_probe": (ctypes.c_int, [vp, vp, i32]),
+        "dm_get_error": (ctypes.c_int, [vp, i32, dp, dp, dp]),
+        "dm_iterations_done": (i64, [vp]),
+        "dm_get_mode_power": (ctypes.c_int, [vp, dp]),
+        "dm_sync": (ctypes.c_int, [vp]),
+        "dm_set_timing": (ctypes.c_int, [vp, i32]),
+        "dm_get_timing": (ctypes.c_int, [vp, i32, dp, P(i64)]),
+        "dm_kernel_name": (ctypes.c_char_p, [i32]),
+        "dm_device_bytes": (ctypes.c_size_t, [vp]),
+        "dm_free": (None, [vp]),
+        "dm_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _is_torch(x):
+    try:
+        import torch
+        return isinstance(x, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        return False
+
+
+def _ptr(x, dtype):
+    """(pointer, mem_kind, keepalive) for a contiguous array of `dtype`."""
+    if _is_torch(x):
+        import torch
+        tdt = {np.float32: torch.float32, np.int32: torch.int32, np.complex64: torch.complex64}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            x = x.to(tdt).contiguous()
+        return x.data_ptr(), (DM_DEVICE if x.is_cuda else DM_HOST), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, DM_HOST, a
+
+
+class Context:
+    """Handle of one dm_ctx plus what must outlive it (allocator hooks)."""
+
+    def __init__(self, handle, params, keep):
+        self.handle = handle
+        self.params = params
+        self._keep = keep
+
+    @property
+    def shape(self):
+        p = self.params
+        return dict(n=p.n, modes=p.modes, views=p.views, obj_h=p.obj_h, obj_w=p.obj_w)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                dm_free(self)
+        except Exception:
+            pass
+
+
+def _check(rc, ctx=None):
+    if rc != DM_OK:
+        lib = load()
+        msg = lib.dm_last_error(ctx.handle if ctx is not None else None)
+        raise DMError(rc, (msg or b"").decode())
+    return rc
+
+
+def _torch_allocator():
+    import torch
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+
+    def _alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=stream)
+        except Exception:
+            return None
+
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return ALLOC_FN(_alloc), FREE_FN(_free), stream
+
+
+# ---------------------------------------------------------------------------
+# the ABI, one function each
+# ---------------------------------------------------------------------------
+def dm_params_default(**kw) -> dm_params:
+    p = dm_params()
+    load().dm_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def dm_init(params: dm_params, positions, intensities, probe0, object0, use_torch_allocator=None,
+            stream=None) -> Context:
+    """Create a context (copies the inputs).  Inputs on a CUDA device are
+    passed as device pointers, otherwise as host pointers; mixing is an
+    error.  With torch CUDA available the context allocates through torch's
+    caching allocator and runs on torch's current stream unless told
+    otherwise."""
+    lib = load()
+    pp, mk0, k0 = _ptr(positions, np.int32)
+    ip, mk1, k1 = _ptr(intensities, np.float32)
+    bp, mk2, k2 = _ptr(probe0, np.complex64)
+    op, mk3, k3 = _ptr(object0, np.complex64)
+    kinds = {mk0, mk1, mk2, mk3}
+    if len(kinds) != 1:
+        raise ValueError("all dm_init inputs must be on the host or all on the device")
+    p = dm_params()
+    ctypes.pointer(p)[0] = params
+    p.mem_kind = kinds.pop()
+    keep = [k0, k1, k2, k3]
+    if use_torch_allocator is None:
+        try:
+            import torch
+            use_torch_allocator = torch.cuda.is_available()
+        except ImportError:  # pragma: no cover
+            use_torch_allocator = False
+    if use_torch_allocator:
+        a, f, tstream = _torch_allocator()
+        p.alloc, p.free = a, f
+        keep += [a, f]
+        if stream is None:
+            stream = tstream.cuda_stream
+    if stream is not None:
+        p.stream = ctypes.c_void_p(int(stream))
+    h = ctypes.c_void_p()
+    rc = lib.dm_init(ctypes.byref(h), ctypes.byref(p), pp, ip, bp, op)
+    _check(rc)
+    return Context(h, p, keep[4:])
+
+
+def dm_iterate(ctx: Context, n_iter: int = 1):
+    return _check(load().dm_iterate(ctx.handle, int(n_iter)), ctx)
+
+
+def dm_run_step(ctx: Context, step: int):
+    return _check(load().dm_run_step(ctx.handle, int(step)), ctx)
+
+
+def _out(ctx, shape, out, device):
+    if out is None:
+        if device:
+            import torch
+            out = torch.empty(shape, dtype=torch.complex64, device="cuda")
+        else:
+            out = np.empty(shape, dtype=np.complex64)
+    if _is_torch(out):
+        if out.dtype.__str__() != "torch.complex64" or not out.is_contiguous():
+            raise ValueError("out must be a contiguous complex64 tensor")
+        return out, out.data_ptr(), (DM_DEVICE if out.is_cuda else DM_HOST)
+    if out.dtype != np.complex64 or not out.flags.c_contiguous:
+        raise ValueError("out must be a contiguous complex64 array")
+    return out, out.ctypes.data, DM_HOST
+
+
+def dm_get_object(ctx: Context, out=None, device=False):
+    p = ctx.params
+    out, ptr, mk = _out(ctx, (p.obj_h, p.obj_w), out, device)
+    _check(load().dm_get_object(ctx.handle, ptr, mk), ctx)
+    return out
+
+
+def dm_get_probe(ctx: Context, out=None, device=False):
+    p = ctx.params
+    out, ptr, mk = _out(ctx, (p.modes, p.n, p.n), out, device)
+    _check(load().dm_get_probe(ctx.handle, ptr, mk), ctx)
+    return out
+
+
+def dm_get_exit_waves(ctx: Context, out=None, device=False):
+    p = ctx.params
+    out, ptr, mk = _out(ctx, (p.views, p.modes, p.n, p.n), out, device)
+    _check(load().dm_get_exit_waves(ctx.handle, ptr, mk), ctx)
+    return out
+
+
+def _set(fn, ctx, arr):
+    ptr, mk, keep = _ptr(arr, np.complex64)
+    _check(fn(ctx.handle, ptr, mk), ctx)
+    del keep
+
+
+def dm_set_exit_waves(ctx: Context, psi):
+    _set(load().dm_set_exit_waves, ctx, psi)
+
+
+def dm_set_object(ctx: Context, obj):
+    _set(load().dm_set_object, ctx, obj)
+
+
+def dm_set_probe(ctx: Context, probe):
+    _set(load().dm_set_probe, ctx, probe)
+
+
+def dm_get_error(ctx: Context, iteration: int = -1):
+    """(eps_obj, eps_probe[M], fourier_err) of one iteration."""
+    eo = ctypes.c_double()
+    ef = ctypes.c_double()
+    ep = (ctypes.c_double * ctx.params.modes)()
+    _check(load().dm_get_error(ctx.handle, int(iteration), ctypes.byref(eo), ep, ctypes.byref(ef)), ctx)
+    return eo.value, list(ep), ef.value
+
+
+def dm_iterations_done(ctx: Context) -> int:
+    return int(load().dm_iterations_done(ctx.handle))
+
+
+def dm_get_mode_power(ctx: Context):
+    out = (ctypes.c_double * ctx.params.modes)()
+    _check(load().dm_get_mode_power(ctx.handle, out), ctx)
+    return list(out)
+
+
+def dm_sync(ctx: Context):
+    return _check(load().dm_sync(ctx.handle), ctx)
+
+
+def dm_set_timing(ctx: Context, enable: bool = True):
+    return _check(load().dm_set_timing(ctx.handle, 1 if enable else 0), ctx)
+
+
+def dm_get_timing(ctx: Context, kernel: int):
+    """(total device ms, launches) of one kernel class."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().dm_get_timing(ctx.handle, int(kernel), ctypes.byref(ms), ctypes.byref(n)), ctx)
+    return ms.value, n.value
+
+
+def dm_kernel_name(kernel: int) -> str:
+    return load().dm_kernel_name(int(kernel)).decode()
+
+
+def dm_device_bytes(ctx: Context) -> int:
+    return int(load().dm_device_bytes(ctx.handle))
+
+
+def dm_free(ctx: Context):
+    if ctx.handle:
+        load().dm_free(ctx.handle)
+        ctx.handle = None
+
+
+def dm_last_error(ctx: Context | None = None) -> str:
+    return (load().dm_last_error(ctx.handle if ctx is not None else None) or b"").decode()
