@@ -1,0 +1,367 @@
+"""Benchmark of the multi-mode difference-map iteration on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one DM iteration (Eq. 3, Eq. 5, Eq. 4, Eq. 6) over every view and
+probe mode of the 8-mode 256x256-frame workload (10,000 views, 2100x2100
+object; synthetic, seeded).  The metric is view*modes processed per second.
+
+* value: device time (CUDA events on the library's stream) of K iterations
+  with every input resident in HBM; the exit waves (42 GB) exceed L2, so no
+  flush is needed between iterations.
+* e2e: the same metric through the C ABI with host (pinned) buffers: dm_init
+  from host memory, K iterations, object/probe/metrics back to the host, all
+  inside the timed region; the bytes are reported per step.
+* roofline: the persistent Fourier-step kernel, the dominant one, timed with
+  CUDA events around each of its launches inside the timed region.
+* cpu_baseline: the FP64 oracle on a bounded sample of the same workload on
+  the host cores.
+* --impl reference: the FP64 oracle itself, timed on the host cores, one
+  bounded sample of views per step (there is no other implementation of the
+  paper's method to run).
+
+With N > 1 (torchrun) every rank runs an independent replica of the workload
+(the method is run on one GPU per scan, no data is exchanged); the time is
+the maximum over ranks and the value counts the views of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "view·modes/s per DM iteration"
+UNIT = "view·modes/s"
+WORKLOAD = "mm256"
+WORKLOAD_DESC = ("8-mode difference map, 256x256 frames, 100x100 scan (10,000 views) at 18 px, "
+                 "2100x2100 object, Hermite-Gauss probe modes, 1e7 photons/frame, FP32")
+KERNELS_PER_ITER = 7   # fourier, obj gather, obj final, probe partial, probe sum, probe div, metrics
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--views", type=int, default=None, help="use only the first V views (small case)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-views", type=int, default=600, help="views in the oracle sample")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_index(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local < len(ids):
+            return ids[local]
+    return local
+
+
+def make_inputs(views, device):
+    import torch
+    from synth import make_scan, initial_guess
+    s = make_scan(WORKLOAD, backend="torch", device=device, views=views)
+    rng = np.random.default_rng(s.meta["seed"] + 1)
+    p0, o0 = initial_guess(s, rng, kind="perturbed")
+    return s, p0.astype(np.complex64), o0.astype(np.complex64)
+
+
+def kernel_source_hash():
+    """Hash of the Fourier-step kernel sources; a stored DRAM-traffic figure
+    is used only while it matches."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("dm_fourier.cu", "dm_fft.cuh", "dm_kernels.h"):
+        with open(os.path.join(ROOT, "paper_1808_10375_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(views):
+    """DRAM bytes of one Fourier-step launch from the committed ncu summary,
+    scaled from its capture size to `views` views, or None if the kernel
+    changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "fourier_mm256_traffic.json")) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d["dram_bytes_per_launch"] * views / d["views"]
+
+
+def fourier_bytes_per_view(n, m):
+    """Algorithmic bytes of the Fourier-step kernel per view: psi read and
+    write (8 B per complex value per mode each), I read (4 B per pixel) and the
+    object-source write (8 B per pixel)."""
+    return (16 * m + 4 + 8) * n * n
+
+
+def iteration_bytes_per_view(n, m):
+    """Algorithmic bytes of one DM iteration per view: psi read and written by
+    the Fourier step, read by the object and by the probe update, I read."""
+    return (32 * m + 4) * n * n
+
+
+def oracle_sample(s, p0, o0, views):
+    """One oracle iteration over the first `views` views (same frames, modes
+    and object); returns seconds."""
+    from oracle import dm as odm
+    import torch
+    pos = s.pos[:views]
+    inten = s.intensities[:views]
+    inten = inten.cpu().numpy() if isinstance(inten, torch.Tensor) else np.asarray(inten)
+    inten = inten.astype(np.float64)
+    p = p0.astype(np.complex128)
+    o = o0.astype(np.complex128)
+    psi = odm.init_exit_waves(p, o, pos)
+    t0 = time.perf_counter()
+    odm.dm_iteration(psi, p, o, pos, inten)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    views = max(1, args.cpu_views // 6)
+    s, p0, o0 = make_inputs(views, dev)
+    m = s.modes
+    for _ in range(args.warmup):
+        oracle_sample(s, p0, o0, views)
+    tot = 0.0
+    for _ in range(args.steps):
+        tot += oracle_sample(s, p0, o0, views)
+    value = views * m * args.steps / tot
+    sample = f"one FP64 oracle iteration over the first {views} views of {WORKLOAD} per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "views_per_step": views, "modes": m, "n": s.n,
+                   "object": list(s.obj_shape)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        pg = tdist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    def max_over_ranks(x):
+        if pg is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_10375_gb300 import dm
+
+    s, p0, o0 = make_inputs(args.views, "cuda")
+    n, m, j = s.n, s.modes, s.views
+    h, w = s.obj_shape
+    params = dm.dm_params_default(n=n, modes=m, views=j, obj_h=h, obj_w=w, beta=0.8)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()          # the library's stream: every kernel and event below
+    torch.cuda.set_stream(stream)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx = dm.dm_init(params, dev(s.pos), s.intensities, dev(p0), dev(o0), stream=stream.cuda_stream)
+    dm.dm_iterate(ctx, args.warmup)
+    dm.dm_sync(ctx)
+
+    # ---- device-timed region -------------------------------------------------
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    dm.dm_set_timing(ctx, True)
+    with ClockSampler(gpu_index(local)) as clk:
+        e0.record(stream)
+        dm.dm_iterate(ctx, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    t_ms = max_over_ranks(e0.elapsed_time(e1))
+    kt = {dm.dm_kernel_name(k): dm.dm_get_timing(ctx, k) for k in range(dm.DM_KERNEL_COUNT)}
+    dm.dm_set_timing(ctx, False)
+    eps_obj, eps_probe, ferr = dm.dm_get_error(ctx)
+    dm.dm_free(ctx)
+    value = world * j * m * args.steps / (t_ms / 1e3)
+
+    f_ms, f_n = kt["fourier"]
+    hbm, peak_kind = peaks()
+    f_bytes = fourier_bytes_per_view(n, m) * j
+    achieved = f_bytes / (f_ms / f_n / 1e3) / 1e9 if f_n else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "traffic": stored_traffic(j),
+                "kernel": "k_fourier (persistent Fourier step, Eq. 3)", "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": f_bytes, "avg_launch_ms": f_ms / f_n if f_n else None}
+    iter_bytes = iteration_bytes_per_view(n, m) * j
+    breakdown = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else None, "launches": v[1],
+                     "share": v[0] / max(1e-9, sum(x[0] for x in kt.values()))} for k, v in kt.items()}
+
+    # ---- end to end through the C ABI with host buffers ---------------------
+    e2e = None
+    if not args.no_e2e:
+        inten_h = torch.empty(s.intensities.shape, dtype=torch.float32, pin_memory=True)
+        inten_h.copy_(s.intensities)
+        pos_h = torch.from_numpy(np.ascontiguousarray(s.pos)).pin_memory()
+        p0_h = torch.from_numpy(p0).pin_memory()
+        o0_h = torch.from_numpy(o0).pin_memory()
+        o_out = torch.empty((h, w), dtype=torch.complex64, pin_memory=True)
+        p_out = torch.empty((m, n, n), dtype=torch.complex64, pin_memory=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = dm.dm_init(params, pos_h, inten_h, p0_h, o0_h, stream=stream.cuda_stream)
+        dm.dm_iterate(c2, args.steps)
+        dm.dm_get_object(c2, out=o_out)
+        dm.dm_get_probe(c2, out=p_out)
+        dm.dm_get_error(c2)
+        t1 = time.perf_counter()
+        dm.dm_free(c2)
+        barrier()
+        e2e_s = max_over_ranks(t1 - t0)
+        h2d = inten_h.numel() * 4 + pos_h.numel() * 4 + p0_h.numel() * 8 + o0_h.numel() * 8
+        d2h = o_out.numel() * 8 + p_out.numel() * 8 + 8 * (2 + m)
+        e2e = {"value": world * j * m * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "session": f"dm_init from pinned host buffers + {args.steps} iterations + object, probe "
+                          f"and metrics to host, per step = session / {args.steps}"}
+
+    # ---- CPU oracle baseline (rank 0, N = 1) ---------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cv = min(args.cpu_views, j)
+        secs = oracle_sample(s, p0, o0, cv)
+        cpu = {"value": cv * m / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 oracle iteration (NumPy, single thread) over the first {cv} views "
+                         f"of the same scan: {secs:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC if args.views is None else f"{WORKLOAD_DESC} (first {j} views)",
+                       "n": n, "modes": m, "views": j, "object": [h, w], "beta": 0.8,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (exit waves %.1f GB)" % (j * m * n * n * 8 / 1e9),
+                       "iteration_algorithmic_bytes": iter_bytes,
+                       "iteration_hbm_frac": iter_bytes / (t_ms / args.steps / 1e3) / 1e9 / hbm},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": KERNELS_PER_ITER * args.steps,
+            "clocks": clk.summary(),
+            "kernels": breakdown,
+            "metrics_last": {"eps_obj": eps_obj, "eps_probe": eps_probe, "fourier_err": ferr},
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

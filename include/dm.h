@@ -102,7 +102,7 @@ typedef struct dm_params {
   dm_free_fn free;
   void* alloc_user;
   void* stream;               /* cudaStream_t, or NULL for a library stream      */
-  int64_t scratch_bytes;      /* L2-resident Fourier-step scratch; 0 = 64 MiB.   */
+  int64_t scratch_bytes;      /* L2-resident Fourier-step scratch; 0 = 96 MiB.   */
                               /* Smaller values mean smaller view chunks.        */
 } dm_params;
 

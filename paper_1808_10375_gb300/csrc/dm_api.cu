@@ -18,7 +18,7 @@
 
 namespace {
 
-constexpr size_t kScratchBudget = 64ull << 20;   // L2-resident Fourier scratch
+constexpr size_t kScratchBudget = 96ull << 20;   // L2-resident Fourier scratch
 constexpr size_t kColumnSmemBudget = 72u << 10;  // column strip in shared memory
 constexpr size_t kColumnTaskBytes = 128u << 10;  // scratch bytes per column task
 constexpr int kFourierLag = 1;                   // stages between task kinds
@@ -270,6 +270,8 @@ int plan_fourier(dm_ctx* c) {
   if (total >= (1ll << 31)) return fail(c, DM_EINVAL, "too many Fourier tasks");
   a.total_tasks = (int)total;
   a.beta = c->p.beta;
+  a.lw = 0;
+  while ((1 << a.lw) < a.w) ++a.lw;
 
   int rc;
   if ((rc = alloc_n(c, &c->scratch, (size_t)a.nslot * B * M * N * N))) return rc;

@@ -25,8 +25,28 @@
 
 namespace dmk {
 
-DM_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-DM_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add/sub.  On sm_100+ devices a single packed f32x2 instruction does
+// both halves (each half is an ordinary round-to-nearest FP32 add).
+DM_HD float2 cadd(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r)
+      : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+  return *reinterpret_cast<float2*>(&r);
+#else
+  return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+DM_HD float2 csub(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r)
+      : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+  return *reinterpret_cast<float2*>(&r);
+#else
+  return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
 DM_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // a * b
 DM_HD float2 cmul(float2 a, float2 b) {

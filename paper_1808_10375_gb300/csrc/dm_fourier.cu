@@ -14,7 +14,8 @@
 // Work items ("tasks"), all with kThreads threads:
 //   R(view, row block): rows of Phi -> forward row DFT -> T in a scratch slot
 //   C(view, strip group): w-column strips of all modes in shared memory ->
-//       forward column DFT, modulus, inverse column DFT, U = beta T'' - T/N
+//       forward column DFT X, modulus, inverse column DFT of (beta s - 1/N^2) X,
+//       which equals U = beta T'' - T/N since T = IDFT_cols(X) / N
 //   I(view, row block): inverse row DFT of U, psi' and the object source
 //       c_j = sum_k conj(P_k) psi'_k (the numerator term of Eq. 5 per view)
 // A CTA takes tasks from a global counter in a software-pipelined order and
@@ -183,24 +184,29 @@ template <int N>
 __device__ __forceinline__ double column_task(const FourierArgs& a, float2* colbuf, const float2* tw,
                                               int j, int jj, int sg, float2* slot) {
   using C = FCfg<N>;
-  const int M = a.M, w = a.w, CS = a.CS;
+  constexpr int LN = Log2<N>::v;
+  const int M = a.M, lw = a.lw, w = 1 << lw, CS = a.CS;
   const int tid = threadIdx.x;
   const float invN = 1.f / (float)N;
+  const float invN2 = invN * invN;
+  const float beta = a.beta;
+  const int tot = M << (LN + lw);
   double ef = 0.0;
   for (int si = 0; si < a.SPG; ++si) {
     const int s = sg * a.SPG + si;
-    const int c0 = s * w;
-    const int tot = M * N * w;
+    const int c0 = s << lw;
     for (int e = tid; e < tot; e += kThreads) {
-      const int c = e % w, y = (e / w) % N, k = e / (w * N);
-      colbuf[(k * w + c) * CS + y + y / C::R2] = __ldcg(slot + (((size_t)jj * M + k) * N + y) * N + c0 + c);
+      const int c = e & (w - 1), y = (e >> lw) & (N - 1), k = e >> (lw + LN);
+      colbuf[(k * w + c) * CS + y + y / C::R2] =
+          __ldcg(slot + ((((size_t)jj * M + k) << LN) + y) * N + c0 + c);
     }
     __syncthreads();
     column_dft<N, false>(colbuf, M * w, CS, tw);
     __syncthreads();
-    const float* ist = a.istrip + ((size_t)j * a.NS + s) * (size_t)w * N;
-    for (int pq = tid; pq < N * w; pq += kThreads) {
-      const int c = pq / N, y = pq % N;
+    // modulus projection fused with the step to U (see the header)
+    const float* ist = a.istrip + (((size_t)j * a.NS + s) << (lw + LN));
+    for (int pq = tid; pq < (N << lw); pq += kThreads) {
+      const int c = pq >> LN, y = pq & (N - 1);
       const int off = c * CS + y + y / C::R2;
       float S = 0.f;
       for (int k = 0; k < M; ++k) S += cnorm(colbuf[k * w * CS + off]);
@@ -209,26 +215,27 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, float2* colb
       const float sc = (S > 0.f) ? (si_ / ss) * invN : 0.f;
       const float dd = fmaf(ss, invN, -si_);
       ef += (double)(dd * dd);
+      const float f = fmaf(beta, sc, -invN2);
       for (int k = 0; k < M; ++k) {
         float2& z = colbuf[k * w * CS + off];
-        z = cscale(z, sc);
+        z = cscale(z, f);
       }
     }
     __syncthreads();
     column_dft<N, true>(colbuf, M * w, CS, tw);
     __syncthreads();
-    const float beta = a.beta;
     for (int e = tid; e < tot; e += kThreads) {
-      const int c = e % w, y = (e / w) % N, k = e / (w * N);
-      float2* gp = slot + (((size_t)jj * M + k) * N + y) * N + c0 + c;
-      const float2 tv = __ldcg(gp);
-      const float2 t2 = colbuf[(k * w + c) * CS + y + y / C::R2];
-      __stcg(gp, make_float2(fmaf(beta, t2.x, -tv.x * invN), fmaf(beta, t2.y, -tv.y * invN)));
+      const int c = e & (w - 1), y = (e >> lw) & (N - 1), k = e >> (lw + LN);
+      __stcg(slot + ((((size_t)jj * M + k) << LN) + y) * N + c0 + c, colbuf[(k * w + c) * CS + y + y / C::R2]);
     }
     __syncthreads();
   }
   return ef;
 }
+
+#ifndef DM_FOURIER_MIN_BLOCKS
+#define DM_FOURIER_MIN_BLOCKS 2
+#endif
 
 template <int N>
 __global__ void __launch_bounds__(kThreads, 2) k_fourier(const FourierArgs a) {

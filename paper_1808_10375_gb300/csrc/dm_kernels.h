@@ -47,7 +47,7 @@ struct FourierArgs {
   int RB;                 // row tasks per view (row blocks)
   int CG;                 // column tasks per view (strip groups)
   int SPG;                // strips per column task
-  int w;                  // strip width (columns)
+  int w, lw;              // strip width (columns)
   int NS;                 // strips per view = N / w
   int CS;                 // shared-memory stride of one column (float2)
   int nstages, total_tasks;

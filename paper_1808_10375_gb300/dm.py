@@ -209,7 +209,9 @@ def dm_init(params: dm_params, positions, intensities, probe0, object0, use_torc
         if stream is None:
             stream = tstream.cuda_stream
     if stream is not None:
-        p.stream = ctypes.c_void_p(int(stream))
+        # handle 0 is the legacy default stream; NULL would ask the library
+        # for a stream of its own, so pass cudaStreamLegacy instead
+        p.stream = ctypes.c_void_p(int(stream) if int(stream) != 0 else 1)
     h = ctypes.c_void_p()
     rc = lib.dm_init(ctypes.byref(h), ctypes.byref(p), pp, ip, bp, op)
     _check(rc)
