@@ -167,6 +167,33 @@ const char* dm_kernel_name(int32_t kernel);
 /* Bytes of device memory the context holds. */
 size_t dm_device_bytes(const dm_ctx* ctx);
 
+/* Probe update (Eq. 4) for callers that cannot allocate device memory, such
+ * as a host application that owns every byte of device memory and gives
+ * this library no allocator, or code that must not call cudaMalloc/cudaFree.
+ * The paper has no counterpart: this entry point exists only for those
+ * callers.  It computes the same result as dm_run_step(DM_STEP_PROBE):
+ *   probe_out_k(u) = sum_j conj(O(r_j+u)) psi_j^k(u) / (sum_j |O(r_j+u)|^2 + delta),
+ *   delta = denom_floor_rel * max_u(denominator); pixels with a zero
+ *   denominator keep probe_in.
+ * All pointers are device pointers on the current device, laid out as for
+ * dm_init (psi [J][M][N][N] complex, object [H][W] complex, positions
+ * [J][2] int32, probes [M][N][N] complex); the caller owns them.
+ * The call allocates nothing: its reduction scratch is one fixed 16 MiB
+ * array inside the library (held by every GPU that loads the library until
+ * the process exits), which bounds the size: about (24 M + 20) N^2 bytes
+ * must fit in 16 MiB (N = 256 allows up to 9 modes).  Larger sizes return
+ * DM_EINVAL.  The first call on a device looks up the array's address; make
+ * it before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race, so order them on one stream.  The positions are
+ * checked on the device first, so the call synchronises `stream`; the
+ * update itself is left enqueued on `stream`.  Errors: DM_EINVAL (sizes,
+ * NULL pointers, a footprint outside the object), DM_ECUDA; the message is
+ * in dm_last_error(NULL). */
+int dm_probe_update_static(const float* psi, const float* object, const int32_t* positions,
+                           const float* probe_in, float* probe_out, int32_t n, int32_t modes,
+                           int32_t views, int32_t obj_h, int32_t obj_w, double denom_floor_rel,
+                           void* stream);
+
 /* Release everything the context holds (NULL is ignored). */
 void dm_free(dm_ctx* ctx);
 

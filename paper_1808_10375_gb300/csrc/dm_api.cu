@@ -420,6 +420,10 @@ int check_ctx(dm_ctx* c) {
 
 }  // namespace
 
+namespace dmk {
+void set_global_error(const char* msg) { g_init_error = msg ? msg : ""; }
+}  // namespace dmk
+
 extern "C" {
 
 void dm_params_default(dm_params* p) {

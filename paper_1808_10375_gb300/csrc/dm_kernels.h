@@ -142,4 +142,7 @@ cudaError_t launch_metrics(const double* ef_part, long long n_ef, const double* 
                            int* status, cudaStream_t s);
 cudaError_t launch_mode_power(const float2* probe, int N, int M, double* out, cudaStream_t s);
 
+// Message returned by dm_last_error(NULL) (calls made without a context).
+void set_global_error(const char* msg);
+
 }  // namespace dmk

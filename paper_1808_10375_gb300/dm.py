@@ -52,7 +52,7 @@ class DMError(RuntimeError):
 EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_object", "dm_get_probe",
            "dm_get_exit_waves", "dm_set_exit_waves", "dm_set_object", "dm_set_probe", "dm_get_error",
            "dm_iterations_done", "dm_get_mode_power", "dm_sync", "dm_set_timing", "dm_get_timing",
-           "dm_kernel_name", "dm_device_bytes", "dm_free", "dm_last_error"]
+           "dm_kernel_name", "dm_device_bytes", "dm_free", "dm_last_error", "dm_probe_update_static"]
 
 _lib = None
 
@@ -88,6 +88,8 @@ def load(path: str = LIB_PATH):
         "dm_device_bytes": (ctypes.c_size_t, [vp]),
         "dm_free": (None, [vp]),
         "dm_last_error": (ctypes.c_char_p, [vp]),
+        "dm_probe_update_static": (ctypes.c_int, [vp, vp, vp, vp, vp, i32, i32, i32, i32, i32,
+                                                  ctypes.c_double, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -332,3 +334,23 @@ def dm_free(ctx: Context):
 
 def dm_last_error(ctx: Context | None = None) -> str:
     return (load().dm_last_error(ctx.handle if ctx is not None else None) or b"").decode()
+
+
+def dm_probe_update_static(psi, obj, positions, probe_in, probe_out, denom_floor_rel=1e-6, stream=None):
+    """Probe update (Eq. 4) that allocates no device memory: for callers that
+    cannot call cudaMalloc (the C call's comment in include/dm.h has the
+    details and the size limit).  All arguments are CUDA tensors:
+    psi [J, M, N, N] complex64, obj [H, W] complex64, positions [J, 2]
+    int32, probe_in / probe_out [M, N, N] complex64."""
+    import torch
+    for t in (psi, obj, positions, probe_in, probe_out):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("dm_probe_update_static takes contiguous CUDA tensors")
+    j, m, n, _ = psi.shape
+    h, w = obj.shape
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = load().dm_probe_update_static(psi.data_ptr(), obj.data_ptr(), positions.data_ptr(), probe_in.data_ptr(),
+                                       probe_out.data_ptr(), n, m, j, h, w, float(denom_floor_rel),
+                                       ctypes.c_void_p(int(stream)))
+    return _check(rc)
