@@ -19,7 +19,7 @@
 namespace {
 
 constexpr size_t kScratchBudget = 96ull << 20;   // L2-resident Fourier scratch
-constexpr size_t kColumnSmemBudget = 72u << 10;  // column strip in shared memory
+constexpr size_t kColumnSmemBudget = 100u << 10; // column strips in shared memory
 constexpr size_t kColumnTaskBytes = 128u << 10;  // scratch bytes per column task
 constexpr int kFourierLag = 1;                   // stages between task kinds
 
@@ -81,6 +81,7 @@ struct dm_ctx {
   size_t counters_bytes = 0;
   int tiles_x = 0, tiles_y = 0, obj_final_blocks = 0;
   CUtensorMap tmap_c;
+  CUtensorMap tmap_s;
   int probe_groups = 0;
   int probe_final_blocks = 0;
   int64_t iters = 0;
@@ -218,18 +219,6 @@ int copy_out(dm_ctx* c, void* dst, const void* src, size_t bytes, int mem_kind) 
 
 bool valid_n(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
 
-// Shared-memory stride of one padded column: N + N/R2 float2 plus a pad that
-// spreads the columns of one warp over distinct banks.
-int column_stride(int N, int R2, int w) {
-  const int base = N + N / R2;
-  int target;
-  if (R2 == 8) target = 8;
-  else if (R2 == 4) target = 4;
-  else target = (w >= 16) ? 1 : (16 / w) % 16;
-  const int pad = ((target - base) % 16 + 16) % 16;
-  return base + pad;
-}
-
 int plan_fourier(dm_ctx* c) {
   const int N = c->N, M = c->M, J = c->J;
   const int R2 = dmk::fourier_r2(N);
@@ -238,12 +227,11 @@ int plan_fourier(dm_ctx* c) {
   dmk::FourierArgs& a = c->fa;
   a.N = N; a.M = M; a.J = J; a.H = c->H; a.W = c->W;
   a.RB = N / GR;
-  int w = N;
-  while (w > 1 && (size_t)M * w * column_stride(N, R2, w) * sizeof(float2) > kColumnSmemBudget) w >>= 1;
-  a.w = w;
-  a.CS = column_stride(N, R2, w);
-  a.NS = N / w;
-  const size_t strip_bytes = (size_t)M * N * w * sizeof(float2);
+  a.w = dmk::kStripW;
+  a.lw = 1;
+  a.NS = N / a.w;
+  const size_t strip_bytes = (size_t)M * N * a.w * sizeof(float2);
+  a.strip_bufs = (2 * (strip_bytes + (size_t)N * a.w * sizeof(float)) <= kColumnSmemBudget) ? 2 : 1;
   int spg = 1;
   while (spg * 2 <= a.NS && strip_bytes * spg * 2 <= kColumnTaskBytes) spg *= 2;
   a.SPG = spg;
@@ -283,7 +271,27 @@ int plan_fourier(dm_ctx* c) {
                              c->stream));
   DM_CUDA(c, cudaStreamSynchronize(c->stream));  // `off` is a host temporary
 
-  c->fsmem = dmk::fourier_smem_bytes(N, M, w, a.CS);
+  // TMA view of the scratch ring for the column tasks: planes of N x N
+  // complex values (8-byte elements), one plane per (view, mode); a box is
+  // kStripW columns x N rows x M modes.
+  {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    DM_CUDA(c, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (!fn || q != cudaDriverEntryPointSuccess) return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const cuuint64_t e = sizeof(float2);
+    const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)a.nslot * B * M};
+    const cuuint64_t strides[2] = {(cuuint64_t)N * e, (cuuint64_t)N * N * e};
+    const cuuint32_t box[3] = {(cuuint32_t)a.w, (cuuint32_t)N, (cuuint32_t)M};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(&c->tmap_s, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, c->scratch, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled (scratch) failed (" + std::to_string((int)r) + ")");
+  }
+  c->fsmem = dmk::fourier_smem_bytes(N, M, a.strip_bufs);
   const int occ = dmk::fourier_occupancy(N, c->fsmem);
   if (occ < 1) return fail(c, DM_ECUDA, "Fourier kernel does not fit on an SM");
   c->fgrid = std::max(1, std::min(a.total_tasks, occ * c->num_sms));
@@ -366,7 +374,7 @@ int run_fourier(dm_ctx* c) {
   c->fa.probe = c->probe[c->cur_P];
   c->fa.obj = c->obj[c->cur_O];
   Timed t(c, DM_KERNEL_FOURIER);
-  DM_CUDA(c, dmk::launch_fourier(c->fa, c->fgrid, c->fsmem, c->stream));
+  DM_CUDA(c, dmk::launch_fourier(&c->tmap_s, c->fa, c->fgrid, c->fsmem, c->stream));
   return DM_OK;
 }
 

@@ -25,8 +25,8 @@
 
 namespace dmk {
 
-// Complex add/sub.  On sm_100+ devices a single packed f32x2 instruction does
-// both halves (each half is an ordinary round-to-nearest FP32 add).
+// Complex add/sub.  On sm_100+ devices one packed f32x2 instruction does both
+// halves (each half is an ordinary round-to-nearest FP32 add).
 DM_HD float2 cadd(float2 a, float2 b) {
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
   unsigned long long r;
@@ -95,30 +95,70 @@ struct Log2 { static constexpr int v = 1 + Log2<R / 2>::v; };
 template <>
 struct Log2<1> { static constexpr int v = 0; };
 
-template <int R>
-DM_HD constexpr int bitrev(int k) {
-  int r = 0;
-  for (int b = 0; b < Log2<R>::v; ++b) r |= ((k >> b) & 1) << (Log2<R>::v - 1 - b);
-  return r;
+
+// Radix-4 butterfly in place (forward: y_k = sum_n a_n (-i)^(nk); INV uses
+// +i).  The multiplication by -+i is folded into the final adds.
+template <bool INV>
+DM_HD void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), d = csub(a1, a3);
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  if (!INV) {
+    a1 = make_float2(t1.x + d.y, t1.y - d.x);
+    a3 = make_float2(t1.x - d.y, t1.y + d.x);
+  } else {
+    a1 = make_float2(t1.x - d.y, t1.y + d.x);
+    a3 = make_float2(t1.x + d.y, t1.y - d.x);
+  }
 }
 
-// In-register R-point DFT (R in {2,4,8,16}) of v[0..R), radix-2 decimation
-// in frequency.  On return v[bitrev<R>(k)] holds X[k].
+// In-register R-point DFT (R in {2, 4, 8, 16}) of v[0..R).  On return
+// v[out_index<R>(k)] holds X[k].
+//   R = 16: 4 x 4 split, X[k1 + 4 k2] at v[4 k1 + k2];
+//   R = 8:  2 x 4 split, X[k1 + 4 k2] at v[2 k1 + k2];
+//   R = 4, 2: natural order.
 template <int R, bool INV>
 DM_HD void dft_reg(float2* v) {
+  if constexpr (R == 2) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if constexpr (R == 4) {
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    // n = 2 n1 + n2: DFT4 over n1 for each n2, twiddle W8^(n2 k1), DFT2 over n2
+    dft4<INV>(v[0], v[2], v[4], v[6]);
+    dft4<INV>(v[1], v[3], v[5], v[7]);
+    v[3] = mul_w16<INV>(v[3], 2);
+    v[5] = mul_w16<INV>(v[5], 4);
+    v[7] = mul_w16<INV>(v[7], 6);
 #pragma unroll
-  for (int half = R / 2; half >= 1; half >>= 1) {
-#pragma unroll
-    for (int b = 0; b < R; b += 2 * half) {
-#pragma unroll
-      for (int i = 0; i < half; ++i) {
-        const float2 a = v[b + i];
-        const float2 c = v[b + i + half];
-        v[b + i] = cadd(a, c);
-        v[b + i + half] = mul_w16<INV>(csub(a, c), i * (16 / (2 * half)));
-      }
+    for (int k1 = 0; k1 < 4; ++k1) {
+      const float2 a = v[2 * k1], b = v[2 * k1 + 1];
+      v[2 * k1] = cadd(a, b);
+      v[2 * k1 + 1] = csub(a, b);
     }
+  } else {
+    // n = 4 n1 + n2: DFT4 over n1 for each n2, twiddle W16^(n2 k1), DFT4 over n2
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+    v[5] = mul_w16<INV>(v[5], 1);
+    v[9] = mul_w16<INV>(v[9], 2);
+    v[13] = mul_w16<INV>(v[13], 3);
+    v[6] = mul_w16<INV>(v[6], 2);
+    v[10] = mul_w16<INV>(v[10], 4);
+    v[14] = mul_w16<INV>(v[14], 6);
+    v[7] = mul_w16<INV>(v[7], 3);
+    v[11] = mul_w16<INV>(v[11], 6);
+    v[15] = mul_w16<INV>(v[15], 9);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
   }
+}
+
+template <int R>
+DM_HD constexpr int out_index(int k) {
+  return R == 16 ? 4 * (k & 3) + (k >> 2) : R == 8 ? 2 * (k & 3) + (k >> 2) : k;
 }
 
 // Split of N into R1 (values per thread) x R2 (threads per transform).
@@ -133,20 +173,20 @@ template <> struct FftShape<256> { static constexpr int R1 = 16, R2 = 16; };
 // twiddled value for k1, Y_t[k1] W_N^(t k1), sits at v[p1_index(k1)].
 // tw[m] = exp(-2 pi i m / N).
 template <int N>
-DM_HD constexpr int p1_index(int k1) { return bitrev<FftShape<N>::R1>(k1); }
+DM_HD constexpr int p1_index(int k1) { return out_index<FftShape<N>::R1>(k1); }
 
 template <int N, bool INV>
 DM_HD void fft_pass1(float2 (&v)[FftShape<N>::R1], int t, const float2* tw) {
   constexpr int R1 = FftShape<N>::R1;
   dft_reg<R1, INV>(v);
 #pragma unroll
-  for (int k1 = 1; k1 < R1; ++k1) v[bitrev<R1>(k1)] = ctw<INV>(v[bitrev<R1>(k1)], tw[t * k1]);
+  for (int k1 = 1; k1 < R1; ++k1) v[out_index<R1>(k1)] = ctw<INV>(v[out_index<R1>(k1)], tw[t * k1]);
 }
 
 // Pass 2 for thread t', in place: u[d*R2 + t] = Y_t[k1 = t' + R2 d] on entry
 // (t < R2, d < R1/R2); on return X[k1 + R1 k2] sits at u[p2_index(d, k2)].
 template <int N>
-DM_HD constexpr int p2_index(int d, int k2) { return d * FftShape<N>::R2 + bitrev<FftShape<N>::R2>(k2); }
+DM_HD constexpr int p2_index(int d, int k2) { return d * FftShape<N>::R2 + out_index<FftShape<N>::R2>(k2); }
 
 template <int N, bool INV>
 DM_HD void fft_pass2(float2 (&u)[FftShape<N>::R1]) {

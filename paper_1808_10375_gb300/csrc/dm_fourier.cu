@@ -22,6 +22,7 @@
 // waits (bounded) on the per-chunk completion counters of what it consumes.
 // Dependencies only point to earlier tasks, which were handed to running CTAs,
 // so the schedule cannot deadlock.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "dm_fft.cuh"
@@ -39,9 +40,12 @@ struct FCfg {
 };
 
 // ------------------------------------------------------------------ R task
+// The 16 lanes of a transform stage their row of psi and of P for the next
+// mode with 16-byte asynchronous copies while the current mode is computed;
+// the row buffers belong to the transform, so only warp-level sync is needed.
 template <int N>
-__device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, const float2* tw, int j,
-                                            int jj, int rb, float2* slot) {
+__device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, float2* stage, const float2* tw,
+                                            int j, int jj, int rb, float2* slot) {
   using C = FCfg<N>;
   const int g = threadIdx.x / C::R2, t = threadIdx.x % C::R2;
   if (g >= C::GR) return;  // whole idle warps (GR * R2 is a multiple of 32)
@@ -49,17 +53,31 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, co
   const int2 p = a.pos[j];
   const float2* orow = a.obj + (size_t)(p.x + y) * a.W + p.y;
   float2* xg = xb + g * C::XB;
+  float2* srow_s = stage + g * N;              // staged psi row
+  float2* prow_s = stage + (C::GR + g) * N;    // staged probe row
+  auto issue = [&](int k) {
+    const float2* src = a.psi + (((size_t)j * a.M + k) * N + y) * N;
+    const float2* psrc = a.probe + ((size_t)k * N + y) * N;
+    for (int q = t; q < N / 2; q += C::R2) {
+      cp_async16(srow_s + 2 * q, src + 2 * q);
+      cp_async16(prow_s + 2 * q, psrc + 2 * q);
+    }
+    cp_async_commit();
+  };
+  issue(0);
   for (int k = 0; k < a.M; ++k) {
-    const float2* prow = a.probe + ((size_t)k * N + y) * N;
-    const float2* srow = a.psi + (((size_t)j * a.M + k) * N + y) * N;
+    cp_async_wait<0>();
+    __syncwarp();
     float2 v[C::R1];
 #pragma unroll
     for (int i = 0; i < C::R1; ++i) {
       const int x = t + C::R2 * i;
-      const float2 po = cmul(__ldg(prow + x), __ldg(orow + x));
-      const float2 s = __ldcs(srow + x);
+      const float2 po = cmul(prow_s[x], __ldg(orow + x));
+      const float2 s = srow_s[x];
       v[i] = make_float2(fmaf(2.f, po.x, -s.x), fmaf(2.f, po.y, -s.y));
     }
+    __syncwarp();
+    if (k + 1 < a.M) issue(k + 1);
     fft_pass1<N, false>(v, t, tw);
     __syncwarp();
 #pragma unroll
@@ -80,8 +98,8 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, co
 
 // ------------------------------------------------------------------ I task
 template <int N>
-__device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, const float2* tw, int j,
-                                            int jj, int rb, const float2* slot) {
+__device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, float2* stage, const float2* tw,
+                                            int j, int jj, int rb, const float2* slot) {
   using C = FCfg<N>;
   const int g = threadIdx.x / C::R2, t = threadIdx.x % C::R2;
   if (g >= C::GR) return;
@@ -89,9 +107,9 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, co
   const int2 p = a.pos[j];
   const float2* orow = a.obj + (size_t)(p.x + y) * a.W + p.y;
   float2* xg = xb + g * C::XB;
-  // c_j accumulator for this row, after the exchange buffers; each thread
-  // owns the positions its pass 2 produces, so no synchronisation is needed.
-  float2* cacc = xb + C::GR * C::XB + g * N;
+  // c_j accumulator for this row; each thread owns the positions its pass 2
+  // produces, so no synchronisation is needed.
+  float2* cacc = stage + g * N;
   const float c2b = 2.f - a.beta;
   for (int k = 0; k < a.M; ++k) {
     const float2* prow = a.probe + ((size_t)k * N + y) * N;
@@ -179,74 +197,165 @@ __device__ __forceinline__ void column_dft(float2* colbuf, int ncol, int CS, con
   }
 }
 
+struct Pipe {          // per-CTA bookkeeping of the shared-memory barriers
+  uint32_t issued[2];  // TMA loads issued on barrier b (one per strip buffer)
+  uint32_t done[2];    // TMA loads waited for
+};
+
+__device__ __forceinline__ void pipe_wait(Pipe& p, uint64_t* bars, int b, int* status) {
+  mbar_wait_bounded(&bars[b], p.done[b] & 1u, status);
+  p.done[b]++;
+}
+
 // ------------------------------------------------------------------ C task
-template <int N>
-__device__ __forceinline__ double column_task(const FourierArgs& a, float2* colbuf, const float2* tw,
-                                              int j, int jj, int sg, float2* slot) {
+// Strips of kStripW columns of every mode move between the row-major scratch
+// and shared memory as 3-D TMA boxes (kStripW x N rows x M modes), laid out
+// [mode][row][column] in shared memory.  The task's strips are double-buffered:
+// the next strip's box and intensities load while the current one is
+// transformed, and U goes back with a TMA store.  Column c of mode k is the
+// stride-kStripW sequence at colbuf + k N kStripW + c; its exchange slots
+// follow the in-place XOR pattern of the row transforms.
+template <int N, bool INV>
+__device__ __forceinline__ void strip_dft(float2* sb, int M, const float2* tw) {
   using C = FCfg<N>;
-  constexpr int LN = Log2<N>::v;
-  const int M = a.M, lw = a.lw, w = 1 << lw, CS = a.CS;
+  constexpr int SW = kStripW;
+  const int g = threadIdx.x / C::R2, t = threadIdx.x % C::R2;
+  const int ncol = M * SW;
+  for (int col0 = 0; col0 < ncol; col0 += C::GROUPS) {
+    const int col = col0 + g;
+    const bool act = col < ncol;
+    const int k = act ? col / SW : 0, c = col % SW;
+    float2* base = sb + k * N * SW + c;
+    float2 v[C::R1];
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < C::R1; ++i) v[i] = base[(t + C::R2 * i) * SW];
+      fft_pass1<N, INV>(v, t, tw);
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int k1 = 0; k1 < C::R1; ++k1) base[(k1 * C::R2 + (t ^ (k1 & (C::R2 - 1)))) * SW] = v[p1_index<N>(k1)];
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int d = 0; d < C::D; ++d)
+#pragma unroll
+        for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = base[((t + C::R2 * d) * C::R2 + (tt ^ t)) * SW];
+      fft_pass2<N, INV>(v);
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int d = 0; d < C::D; ++d)
+#pragma unroll
+        for (int k2 = 0; k2 < C::R2; ++k2) base[(t + C::R2 * d + C::R1 * k2) * SW] = v[p2_index<N>(d, k2)];
+    }
+    __syncwarp();
+  }
+}
+
+template <int N>
+__device__ __forceinline__ double column_task(const FourierArgs& a, const CUtensorMap* tmap, float2* sbuf,
+                                              float* ibuf, const float2* tw, uint64_t* bars, Pipe& pp, int j,
+                                              int zview, int sg) {
+  constexpr int SW = kStripW;
+  const int M = a.M;
   const int tid = threadIdx.x;
   const float invN = 1.f / (float)N;
   const float invN2 = invN * invN;
   const float beta = a.beta;
-  const int tot = M << (LN + lw);
-  double ef = 0.0;
+  const int nbuf = a.strip_bufs;
+  const uint32_t strip_elems = (uint32_t)M * N * SW;
+  const uint32_t strip_bytes = strip_elems * (uint32_t)sizeof(float2);
+  float ef = 0.f;  // this thread's few terms; the cross-thread sums are FP64
+  auto issue = [&](int si) {  // strip si of the task into buffer si % nbuf (all threads)
+    const int s = sg * a.SPG + si;
+    const int b = si % nbuf;
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&bars[b], strip_bytes);
+      tma_load_3d(sbuf + (size_t)b * strip_elems, tmap, s * SW, 0, zview, &bars[b]);
+    }
+    pp.issued[b]++;
+    const float* ist = a.istrip + ((size_t)j * a.NS + s) * (N * SW);
+    for (int q = tid; q < (N * SW) / 4; q += kThreads) cp_async16(ibuf + b * (N * SW) + 4 * q, ist + 4 * q);
+    cp_async_commit();
+  };
+  if (tid == 0) fence_proxy_async_global();
+  issue(0);
+  if (nbuf > 1 && a.SPG > 1) issue(1);
   for (int si = 0; si < a.SPG; ++si) {
     const int s = sg * a.SPG + si;
-    const int c0 = s << lw;
-    for (int e = tid; e < tot; e += kThreads) {
-      const int c = e & (w - 1), y = (e >> lw) & (N - 1), k = e >> (lw + LN);
-      colbuf[(k * w + c) * CS + y + y / C::R2] =
-          __ldcg(slot + ((((size_t)jj * M + k) << LN) + y) * N + c0 + c);
-    }
+    const int b = si % nbuf;
+    float2* sb = sbuf + (size_t)b * strip_elems;
+    const float* ib = ibuf + b * (N * SW);
+    if (tid == 0) pipe_wait(pp, bars, b, a.status);
+    else pp.done[b]++;
     __syncthreads();
-    column_dft<N, false>(colbuf, M * w, CS, tw);
+    strip_dft<N, false>(sb, M, tw);
+    if (nbuf > 1 && si + 1 < a.SPG) cp_async_wait<1>(); else cp_async_wait<0>();
     __syncthreads();
     // modulus projection fused with the step to U (see the header)
-    const float* ist = a.istrip + (((size_t)j * a.NS + s) << (lw + LN));
-    for (int pq = tid; pq < (N << lw); pq += kThreads) {
-      const int c = pq >> LN, y = pq & (N - 1);
-      const int off = c * CS + y + y / C::R2;
+    for (int pq = tid; pq < N * SW; pq += kThreads) {
+      const int y = pq / SW, c = pq % SW;   // ibuf is [column][row]
       float S = 0.f;
-      for (int k = 0; k < M; ++k) S += cnorm(colbuf[k * w * CS + off]);
-      const float si_ = sqrtf(__ldcs(ist + pq));
+      for (int k = 0; k < M; ++k) S += cnorm(sb[k * N * SW + pq]);
+      const float si_ = sqrtf(ib[c * N + y]);
       const float ss = sqrtf(S);
       const float sc = (S > 0.f) ? (si_ / ss) * invN : 0.f;
       const float dd = fmaf(ss, invN, -si_);
-      ef += (double)(dd * dd);
+      ef = fmaf(dd, dd, ef);
       const float f = fmaf(beta, sc, -invN2);
       for (int k = 0; k < M; ++k) {
-        float2& z = colbuf[k * w * CS + off];
+        float2& z = sb[k * N * SW + pq];
         z = cscale(z, f);
       }
     }
     __syncthreads();
-    column_dft<N, true>(colbuf, M * w, CS, tw);
+    strip_dft<N, true>(sb, M, tw);
+    fence_proxy_async_smem();
     __syncthreads();
-    for (int e = tid; e < tot; e += kThreads) {
-      const int c = e & (w - 1), y = (e >> lw) & (N - 1), k = e >> (lw + LN);
-      __stcg(slot + ((((size_t)jj * M + k) << LN) + y) * N + c0 + c, colbuf[(k * w + c) * CS + y + y / C::R2]);
+    if (tid == 0) {
+      tma_store_3d(tmap, s * SW, 0, zview, sb);
+      bulk_commit();
     }
-    __syncthreads();
+    const int nxt = si + nbuf;
+    if (nxt < a.SPG) {
+      if (tid == 0) bulk_wait_read<0>();  // the store has left buffer b
+      __syncthreads();
+      issue(nxt);
+    }
   }
-  return ef;
+  return (double)ef;
 }
 
-#ifndef DM_FOURIER_MIN_BLOCKS
-#define DM_FOURIER_MIN_BLOCKS 2
-#endif
-
 template <int N>
-__global__ void __launch_bounds__(kThreads, 2) k_fourier(const FourierArgs a) {
+__global__ void __launch_bounds__(kThreads, 2)
+    k_fourier(const __grid_constant__ CUtensorMap tmap, const FourierArgs a) {
   using C = FCfg<N>;
-  extern __shared__ __align__(16) float2 smem[];
-  float2* tw = smem;
-  float2* work = smem + N;
+  extern __shared__ unsigned char smem_raw[];
+  // 128-byte aligned base (TMA boxes land at 128-byte aligned addresses)
+  float2* tw = reinterpret_cast<float2*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+  float2* work = tw + kTwBytes / sizeof(float2);
+  // row tasks: exchange buffers, then two row buffers per transform (staged
+  // psi and P rows of R; the object-source accumulator of I); column tasks:
+  // the strip buffers, then their intensities
+  float2* xb = work;
+  float2* stage = work + C::GR * C::XB;
+  float2* sbuf = work;
+  float* ibuf = reinterpret_cast<float*>(work + (size_t)a.strip_bufs * a.M * N * kStripW);
+  __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_task;
   __shared__ int s_skip;
   __shared__ double s_red[kThreads / 32];
   for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  Pipe pp = {{0, 0}, {0, 0}};
 
   int* disp = a.counters;
   int* doneR = a.counters + 1;
@@ -305,14 +414,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_fourier(const FourierArgs a) {
     __syncthreads();
 
     if (!s_skip) {
-      float2* slot = a.scratch + (size_t)(c % a.nslot) * slot_elems;
+      const int sl = c % a.nslot;
+      float2* slot = a.scratch + (size_t)sl * slot_elems;
       if (kind == 0) {
         const int jj = local / a.RB, rb = local % a.RB;
-        row_forward<N>(a, work, tw, c * a.B + jj, jj, rb, slot);
+        row_forward<N>(a, xb, stage, tw, c * a.B + jj, jj, rb, slot);
       } else if (kind == 1) {
         const int jj = local / a.CG, sg = local % a.CG;
         const int j = c * a.B + jj;
-        double ef = column_task<N>(a, work, tw, j, jj, sg, slot);
+        double ef = column_task<N>(a, &tmap, sbuf, ibuf, tw, bars, pp, j, (sl * a.B + jj) * a.M, sg);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ef += __shfl_xor_sync(0xffffffffu, ef, o);
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = ef;
@@ -324,12 +434,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_fourier(const FourierArgs a) {
         }
       } else {
         const int jj = local / a.RB, rb = local % a.RB;
-        row_inverse<N>(a, work, tw, c * a.B + jj, jj, rb, slot);
+        row_inverse<N>(a, xb, stage, tw, c * a.B + jj, jj, rb, slot);
       }
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd((kind == 0 ? doneR : kind == 1 ? doneC : doneI) + c, 1);
+    if (threadIdx.x == 0) {
+      bulk_wait<0>();   // TMA stores of the task have landed
+      __threadfence();
+      atomicAdd((kind == 0 ? doneR : kind == 1 ? doneC : doneI) + c, 1);
+    }
+  }
+  // Copies that a timed-out wait left in flight must land before the CTA exits.
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b)
+      while (pp.done[b] < pp.issued[b]) pipe_wait(pp, bars, b, a.status);
+    bulk_wait<0>();
   }
 }
 
@@ -345,34 +465,31 @@ int fourier_r2(int N) {
 }
 
 template <int N>
-static size_t smem_for(int M, int w, int CS) {
+static size_t smem_for(int M, int bufs) {
   using C = FCfg<N>;
-  const size_t rows = (size_t)C::GR * (C::XB + N);
-  const size_t cols = (size_t)M * w * CS;
-  return sizeof(float2) * (N + (rows > cols ? rows : cols));
+  const size_t rows = (size_t)C::GR * (C::XB + 2 * N);
+  const size_t cols = (size_t)bufs * M * N * kStripW + (size_t)bufs * N * kStripW / 2;
+  return 128 + kTwBytes + sizeof(float2) * (rows > cols ? rows : cols);
 }
 
-size_t fourier_smem_bytes(int N, int M, int w, int CS) {
+size_t fourier_smem_bytes(int N, int M, int bufs) {
   switch (N) {
-    case 16: return smem_for<16>(M, w, CS);
-    case 32: return smem_for<32>(M, w, CS);
-    case 64: return smem_for<64>(M, w, CS);
-    case 128: return smem_for<128>(M, w, CS);
-    case 256: return smem_for<256>(M, w, CS);
+    case 16: return smem_for<16>(M, bufs);
+    case 32: return smem_for<32>(M, bufs);
+    case 64: return smem_for<64>(M, bufs);
+    case 128: return smem_for<128>(M, bufs);
+    case 256: return smem_for<256>(M, bufs);
     default: return 0;
   }
 }
 
-template <int N>
-static const void* kernel_ptr() { return (const void*)k_fourier<N>; }
-
 static const void* fourier_kernel(int N) {
   switch (N) {
-    case 16: return kernel_ptr<16>();
-    case 32: return kernel_ptr<32>();
-    case 64: return kernel_ptr<64>();
-    case 128: return kernel_ptr<128>();
-    case 256: return kernel_ptr<256>();
+    case 16: return (const void*)k_fourier<16>;
+    case 32: return (const void*)k_fourier<32>;
+    case 64: return (const void*)k_fourier<64>;
+    case 128: return (const void*)k_fourier<128>;
+    case 256: return (const void*)k_fourier<256>;
     default: return nullptr;
   }
 }
@@ -387,13 +504,14 @@ int fourier_occupancy(int N, size_t smem) {
   return nb;
 }
 
-cudaError_t launch_fourier(const FourierArgs& a, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_fourier(const void* tmap, const FourierArgs& a, int grid, size_t smem, cudaStream_t s) {
+  const CUtensorMap& m = *static_cast<const CUtensorMap*>(tmap);
   switch (a.N) {
-    case 16: k_fourier<16><<<grid, kThreads, smem, s>>>(a); break;
-    case 32: k_fourier<32><<<grid, kThreads, smem, s>>>(a); break;
-    case 64: k_fourier<64><<<grid, kThreads, smem, s>>>(a); break;
-    case 128: k_fourier<128><<<grid, kThreads, smem, s>>>(a); break;
-    case 256: k_fourier<256><<<grid, kThreads, smem, s>>>(a); break;
+    case 16: k_fourier<16><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 32: k_fourier<32><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 64: k_fourier<64><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 128: k_fourier<128><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 256: k_fourier<256><<<grid, kThreads, smem, s>>>(m, a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

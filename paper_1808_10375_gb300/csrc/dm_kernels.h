@@ -18,6 +18,8 @@ enum : int {
 constexpr int kThreads = 256;          // threads per CTA of every hot kernel
 constexpr int kMetricsRing = 1024;     // iterations of metrics kept on the device
 constexpr int kMaxModes = 16;
+constexpr int kStripW = 2;             // columns per Fourier column strip
+constexpr int kTwBytes = 2048;         // shared twiddle table (N <= 256 complex values)
 
 // ---------------------------------------------------------------------------
 // Fourier step (Eq. 3): one persistent launch over all views.
@@ -47,9 +49,9 @@ struct FourierArgs {
   int RB;                 // row tasks per view (row blocks)
   int CG;                 // column tasks per view (strip groups)
   int SPG;                // strips per column task
-  int w, lw;              // strip width (columns)
+  int w, lw;              // strip width (columns, = kStripW) and its log2
   int NS;                 // strips per view = N / w
-  int CS;                 // shared-memory stride of one column (float2)
+  int strip_bufs;         // strip buffers of a column task (1 or 2)
   int nstages, total_tasks;
   const int* stage_off;   // [nstages + 1] first task of each stage
   int* counters;          // [0] dispenser, then done R/C/I per chunk
@@ -117,8 +119,8 @@ struct ProbeFinalArgs {
 };
 
 // Launchers (return the launch error).
-cudaError_t launch_fourier(const FourierArgs& a, int grid, size_t smem, cudaStream_t s);
-size_t fourier_smem_bytes(int N, int M, int w, int CS);
+cudaError_t launch_fourier(const void* tmap, const FourierArgs& a, int grid, size_t smem, cudaStream_t s);
+size_t fourier_smem_bytes(int N, int M, int bufs);
 int fourier_occupancy(int N, size_t smem);
 int fourier_r2(int N);
 

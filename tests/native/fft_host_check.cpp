@@ -70,7 +70,7 @@ static double check_reg(std::mt19937_64& rng) {
       re += x[n].x * std::cos(a) - x[n].y * std::sin(a);
       im += x[n].x * std::sin(a) + x[n].y * std::cos(a);
     }
-    const float2 g = v[bitrev<R>(k)];
+    const float2 g = v[out_index<R>(k)];
     num += (g.x - re) * (g.x - re) + (g.y - im) * (g.y - im);
     den += re * re + im * im;
   }
