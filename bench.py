@@ -185,6 +185,32 @@ def iteration_bytes_per_view(n, m):
     return (32 * m + 4) * n * n
 
 
+def rank_collectives(pg, device):
+    """(barrier, max_over_ranks) for the replicas: every rank times its own
+    replica and the job's time is the slowest rank's.  ``pg`` is
+    torch.distributed (any backend) or None for one process."""
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    def max_over_ranks(x):
+        if pg is None:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    return barrier, max_over_ranks
+
+
+def job_throughput(world, views, modes, steps, seconds):
+    """view*modes per second of the whole job: every rank advances its own
+    replica of ``views`` views by ``steps`` iterations in ``seconds`` (the
+    maximum over ranks)."""
+    return world * views * modes * steps / seconds
+
+
 def oracle_sample(s, p0, o0, views):
     """One oracle iteration over the first `views` views (same frames, modes
     and object); returns seconds."""
@@ -243,16 +269,7 @@ def main():
         tdist.init_process_group("nccl")
         pg = tdist
 
-    def barrier():
-        if pg is not None:
-            pg.barrier()
-
-    def max_over_ranks(x):
-        if pg is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = rank_collectives(pg, "cuda")
 
     import __graft_entry__
     __graft_entry__.build()
@@ -287,7 +304,7 @@ def main():
     dm.dm_set_timing(ctx, False)
     eps_obj, eps_probe, ferr = dm.dm_get_error(ctx)
     dm.dm_free(ctx)
-    value = world * j * m * args.steps / (t_ms / 1e3)
+    value = job_throughput(world, j, m, args.steps, t_ms / 1e3)
 
     f_ms, f_n = kt["fourier"]
     hbm, peak_kind = peaks()
@@ -325,7 +342,7 @@ def main():
         e2e_s = max_over_ranks(t1 - t0)
         h2d = inten_h.numel() * 4 + pos_h.numel() * 4 + p0_h.numel() * 8 + o0_h.numel() * 8
         d2h = o_out.numel() * 8 + p_out.numel() * 8 + 8 * (2 + m)
-        e2e = {"value": world * j * m * args.steps / e2e_s, "unit": UNIT,
+        e2e = {"value": job_throughput(world, j, m, args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "session": f"dm_init from pinned host buffers + {args.steps} iterations + object, probe "
                           f"and metrics to host, per step = session / {args.steps}"}

@@ -142,6 +142,46 @@ def object_update(psi, probe, obj, pos, delta_rel):
     return new
 
 
+def object_denominator(probe, pos, shape):
+    """The denominator of Eq. 5 over the whole object array,
+    sum_j sum_k |P_k(r - r_j)|^2, accumulated one footprint at a time."""
+    n = probe.shape[-1]
+    den = np.zeros(shape, dtype=np.float64)
+    p2 = np.sum(np.abs(probe) ** 2, axis=0)
+    for j in range(pos.shape[0]):
+        r, c = int(pos[j, 0]), int(pos[j, 1])
+        den[r:r + n, c:c + n] += p2
+    return den
+
+
+def views_covering(pos, n, pixel):
+    """Indices j of the footprints that contain the object pixel (row, col)."""
+    r, c = pixel
+    inside = (pos[:, 0] <= r) & (r < pos[:, 0] + n) & (pos[:, 1] <= c) & (c < pos[:, 1] + n)
+    return np.nonzero(inside)[0]
+
+
+def object_update_at(pixels, psi_of_view, probe, obj, pos, delta_rel, den_max):
+    """Eq. 5 evaluated at a few object pixels only, for scans too large for
+    ``object_update``.  ``psi_of_view(j)`` returns the [M, N, N] exit waves of
+    view j; ``den_max`` is the maximum of ``object_denominator`` over the
+    whole array (it fixes delta).  Pixels no footprint covers keep their
+    value.  Returns the new object values at ``pixels``."""
+    n = probe.shape[-1]
+    delta = delta_rel * den_max
+    out = np.empty(len(pixels), dtype=np.complex128)
+    for i, (r, c) in enumerate(pixels):
+        num = 0.0 + 0.0j
+        den = 0.0
+        for j in views_covering(pos, n, (r, c)):
+            u, v = r - int(pos[j, 0]), c - int(pos[j, 1])
+            pk = probe[:, u, v]
+            num += np.sum(np.conj(pk) * psi_of_view(j)[:, u, v])
+            den += float(np.sum(np.abs(pk) ** 2))
+        out[i] = num / (den + delta) if den > 0 else obj[r, c]
+    return out
+
+
 def probe_update(psi, probe, obj, pos, delta_rel):
     """Eq. 4 with one object mode, for every probe mode k:
         P_k(u) = sum_j conj(O(r_j + u)) psi_j^k(u)

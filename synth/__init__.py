@@ -7,8 +7,10 @@ and it holds none of the difference-map iteration itself.
 """
 from .scan import (WORKLOADS, Scan, make_scan, grf_object, gaussian_probe,
                    hg_probe_modes, raster_positions, simulate_intensities,
-                   initial_guess, random_exit_waves)
+                   initial_guess, random_exit_waves,
+                   random_exit_waves_device)
 
 __all__ = ["WORKLOADS", "Scan", "make_scan", "grf_object", "gaussian_probe",
            "hg_probe_modes", "raster_positions", "simulate_intensities",
-           "initial_guess", "random_exit_waves"]
+           "initial_guess", "random_exit_waves",
+           "random_exit_waves_device"]

@@ -272,3 +272,32 @@ def random_exit_waves(probe, obj, pos, rng: np.random.Generator, rel=0.3):
         noise = rng.standard_normal(prod.shape) + 1j * rng.standard_normal(prod.shape)
         out[j] = prod + rel * np.abs(prod).mean() * noise
     return out
+
+
+def random_exit_waves_device(probe, obj, pos, seed, rel=0.3, device="cuda", chunk=256):
+    """Device counterpart of ``random_exit_waves`` for scans too large for
+    the host: psi_j = P_k O_patch_j + rel * mean|P O_patch_j| * (a + i b) with
+    a, b standard normal from a torch.Generator seeded with ``seed``.
+    ``probe`` and ``obj`` are complex64 arrays; returns a complex64 tensor
+    [J, M, N, N] on ``device``."""
+    import torch
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed))
+    p_t = torch.as_tensor(np.ascontiguousarray(probe, np.complex64)).to(dev)
+    o_t = torch.as_tensor(np.ascontiguousarray(obj, np.complex64)).to(dev)
+    n = p_t.shape[-1]
+    j_total = pos.shape[0]
+    out = torch.empty((j_total,) + tuple(p_t.shape), dtype=torch.complex64, device=dev)
+    ar = torch.arange(n, device=dev)
+    pos_t = torch.from_numpy(pos.astype(np.int64)).to(dev)
+    for j0 in range(0, j_total, chunk):
+        j1 = min(j_total, j0 + chunk)
+        rr = pos_t[j0:j1, 0][:, None, None] + ar[None, :, None]
+        cc = pos_t[j0:j1, 1][:, None, None] + ar[None, None, :]
+        prod = p_t[None] * o_t[rr, cc][:, None]                      # [b, M, n, n]
+        scale = rel * prod.abs().mean(dim=(1, 2, 3), keepdim=True)
+        re = torch.randn(prod.shape, generator=gen, device=dev, dtype=torch.float32)
+        im = torch.randn(prod.shape, generator=gen, device=dev, dtype=torch.float32)
+        out[j0:j1] = prod + scale * torch.complex(re, im)
+    return out

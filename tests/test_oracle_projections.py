@@ -126,3 +126,42 @@ def test_denominator_floor_closed_form():
     for d in (0.0, 0.25):
         pn = dm.probe_update(psi, probe, obj, pos, d)
         np.testing.assert_allclose(pn[0], np.conj(o) * psi[0, 0] / (abs(o) ** 2 * (1 + d)), rtol=1e-14)
+
+
+def test_sampled_object_update_fixed_point_and_uncovered_pixels():
+    # Eq. 5 at single pixels: consistent waves give back the object on
+    # covered pixels; uncovered pixels keep the starting value.
+    rng = np.random.default_rng(8)
+    probe, obj, pos, psi = consistent_state(rng, m=3)
+    start = rand_c(rng, obj.shape)
+    n = probe.shape[-1]
+    cov = covered(obj.shape, pos, n)
+    pix = [tuple(p) for p in np.argwhere(cov)[::7]] + [tuple(p) for p in np.argwhere(~cov)]
+    den = dm.object_denominator(probe, pos, obj.shape)
+    got = dm.object_update_at(pix, lambda j: psi[j], probe, start, pos, 0.0, den.max())
+    for (r, c), g in zip(pix, got):
+        if cov[r, c]:
+            assert g == pytest.approx(obj[r, c], rel=1e-12)
+        else:
+            assert g == start[r, c]
+
+
+def test_sampled_object_update_closed_form_and_whole_array_agreement():
+    # one uniform view: O = conj(p) psi / (|p|^2 (1 + delta_rel)) at every pixel
+    n = 4
+    p = 0.6 - 0.8j
+    probe = np.full((1, n, n), p)
+    rng = np.random.default_rng(9)
+    psi = rand_c(rng, (1, 1, n, n))
+    pos = np.array([[0, 0]], np.int32)
+    pix = [(r, c) for r in range(n) for c in range(n)]
+    got = dm.object_update_at(pix, lambda j: psi[j], probe, np.zeros((n, n), complex), pos, 0.5, abs(p) ** 2)
+    np.testing.assert_allclose(got, (np.conj(p) * psi[0, 0] / (abs(p) ** 2 * 1.5)).ravel(), rtol=1e-14)
+    # on a generic state it agrees with the whole-array update
+    probe, obj, pos, _ = consistent_state(rng, m=2)
+    psi = rand_c(rng, (len(pos),) + probe.shape)
+    full = dm.object_update(psi, probe, obj, pos, 1e-3)
+    den = dm.object_denominator(probe, pos, obj.shape)
+    pix = [(r, c) for r in range(obj.shape[0]) for c in range(obj.shape[1])]
+    got = dm.object_update_at(pix, lambda j: psi[j], probe, obj, pos, 1e-3, den.max())
+    np.testing.assert_allclose(got, full.ravel(), rtol=1e-12)
