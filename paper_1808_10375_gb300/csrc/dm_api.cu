@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -231,7 +232,12 @@ int plan_fourier(dm_ctx* c) {
   a.lw = 1;
   a.NS = N / a.w;
   const size_t strip_bytes = (size_t)M * N * a.w * sizeof(float2);
-  a.strip_bufs = (2 * (strip_bytes + (size_t)N * a.w * sizeof(float)) <= kColumnSmemBudget) ? 2 : 1;
+  // Two strip buffers while they fit the budget; a third only where it does
+  // not enlarge the CTA beyond what the row tasks need (shared memory taken
+  // from L1 slows the row tasks, which read the object through L1).
+  a.strip_bufs = 2 * (strip_bytes + (size_t)N * a.w * sizeof(float)) <= kColumnSmemBudget ? 2 : 1;
+  if (a.strip_bufs == 2 && dmk::fourier_smem_bytes(N, M, 3) <= dmk::fourier_smem_bytes(N, M, 1))
+    a.strip_bufs = 3;
   int spg = 1;
   while (spg * 2 <= a.NS && strip_bytes * spg * 2 <= kColumnTaskBytes) spg *= 2;
   a.SPG = spg;
@@ -291,6 +297,11 @@ int plan_fourier(dm_ctx* c) {
     if (r != CUDA_SUCCESS)
       return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled (scratch) failed (" + std::to_string((int)r) + ")");
   }
+  // a second strip buffer is only worth it while it costs no resident CTA
+  while (a.strip_bufs > 1 &&
+         dmk::fourier_occupancy(N, dmk::fourier_smem_bytes(N, M, a.strip_bufs)) <
+             dmk::fourier_occupancy(N, dmk::fourier_smem_bytes(N, M, a.strip_bufs - 1)))
+    --a.strip_bufs;
   c->fsmem = dmk::fourier_smem_bytes(N, M, a.strip_bufs);
   const int occ = dmk::fourier_occupancy(N, c->fsmem);
   if (occ < 1) return fail(c, DM_ECUDA, "Fourier kernel does not fit on an SM");
@@ -354,8 +365,11 @@ int plan_object(dm_ctx* c, const std::vector<int32_t>& hpos) {
 
 int plan_probe(dm_ctx* c) {
   const int nn = c->N * c->N;
-  const int utiles = (nn + dmk::kProbePxPerCta - 1) / dmk::kProbePxPerCta;
-  int g = (4 * c->num_sms + utiles - 1) / utiles;
+  const int tp = dmk::probe_tile_px(c->M);
+  const int tiles = (nn + tp - 1) / tp;
+  // view groups such that tiles x groups work items split evenly over one
+  // persistent CTA per SM
+  int g = c->num_sms / std::gcd(tiles, c->num_sms);
   g = std::max(1, std::min(g, c->J));
   c->probe_groups = g;
   c->probe_final_blocks = std::max(1, std::min((nn + dmk::kThreads - 1) / dmk::kThreads, 256));
@@ -403,9 +417,10 @@ int run_probe(dm_ctx* c, const float2* o) {
   dmk::ProbePartialArgs a{};
   a.N = c->N; a.M = c->M; a.J = c->J; a.H = c->H; a.W = c->W; a.groups = c->probe_groups;
   a.psi = c->psi; a.obj = o; a.pos = c->pos; a.part_num = c->part_num; a.part_den = c->part_den;
+  a.status = c->status;
   {
     Timed t(c, DM_KERNEL_PROBE_PARTIAL);
-    DM_CUDA(c, dmk::launch_probe_partial(a, c->stream));
+    DM_CUDA(c, dmk::launch_probe_partial(a, c->num_sms, c->stream));
   }
   DM_CUDA(c, cudaMemsetAsync(c->dmax_P, 0, sizeof(unsigned long long), c->stream));
   dmk::ProbeFinalArgs f{};

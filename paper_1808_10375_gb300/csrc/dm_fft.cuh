@@ -4,8 +4,8 @@
 // of R2 threads that each hold R1 complex values:
 //   pass 1: thread t transforms x[t + R2*i], i < R1, in registers (an R1-point
 //           DFT), then multiplies output k1 by W_N^(t*k1);
-//   exchange through a small shared buffer laid out [k1][t] with one float2
-//           of padding per row (bank-conflict free for both access patterns);
+//   exchange through a small shared buffer laid out [k1][t ^ (k1 mod R2)]
+//           (the XOR swizzle keeps both access patterns bank-conflict free);
 //   pass 2: thread t' transforms, for each k1 = t' + R2*d (d < R1/R2), the R2
 //           values over t, producing X[k1 + R1*k2].
 // This is the Cooley-Tukey split X[k1 + R1 k2] =

@@ -36,7 +36,7 @@ struct FCfg {
   static constexpr int R1 = FftShape<N>::R1, R2 = FftShape<N>::R2, D = R1 / R2;
   static constexpr int GROUPS = kThreads / R2;          // transforms in flight per CTA
   static constexpr int GR = GROUPS < N ? GROUPS : N;     // rows per row task
-  static constexpr int XB = R1 * (R2 + 1);               // exchange buffer per transform
+  static constexpr int XB = R1 * R2;                     // exchange buffer per transform (= N)
 };
 
 // ------------------------------------------------------------------ R task
@@ -81,12 +81,12 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, fl
     fft_pass1<N, false>(v, t, tw);
     __syncwarp();
 #pragma unroll
-    for (int k1 = 0; k1 < C::R1; ++k1) xg[k1 * (C::R2 + 1) + t] = v[p1_index<N>(k1)];
+    for (int k1 = 0; k1 < C::R1; ++k1) xg[k1 * C::R2 + (t ^ (k1 & (C::R2 - 1)))] = v[p1_index<N>(k1)];
     __syncwarp();
 #pragma unroll
     for (int d = 0; d < C::D; ++d)
 #pragma unroll
-      for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = xg[(t + C::R2 * d) * (C::R2 + 1) + tt];
+      for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = xg[(t + C::R2 * d) * C::R2 + (tt ^ t)];
     fft_pass2<N, false>(v);
     float2* trow = slot + (((size_t)jj * a.M + k) * N + y) * N;
 #pragma unroll
@@ -121,12 +121,12 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, fl
     fft_pass1<N, true>(v, t, tw);
     __syncwarp();
 #pragma unroll
-    for (int k1 = 0; k1 < C::R1; ++k1) xg[k1 * (C::R2 + 1) + t] = v[p1_index<N>(k1)];
+    for (int k1 = 0; k1 < C::R1; ++k1) xg[k1 * C::R2 + (t ^ (k1 & (C::R2 - 1)))] = v[p1_index<N>(k1)];
     __syncwarp();
 #pragma unroll
     for (int d = 0; d < C::D; ++d)
 #pragma unroll
-      for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = xg[(t + C::R2 * d) * (C::R2 + 1) + tt];
+      for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = xg[(t + C::R2 * d) * C::R2 + (tt ^ t)];
     fft_pass2<N, true>(v);
 #pragma unroll
     for (int d = 0; d < C::D; ++d) {
@@ -153,53 +153,9 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, fl
     }
 }
 
-// Column DFTs of `ncol` padded columns in shared memory (column c starts at
-// c * CS; row y sits at y + y / R2).  The exchange between the two passes
-// reuses the column's own storage.
-template <int N, bool INV>
-__device__ __forceinline__ void column_dft(float2* colbuf, int ncol, int CS, const float2* tw) {
-  using C = FCfg<N>;
-  const int g = threadIdx.x / C::R2, t = threadIdx.x % C::R2;
-  for (int col0 = 0; col0 < ncol; col0 += C::GROUPS) {
-    const int col = col0 + g;
-    const bool act = col < ncol;
-    float2* base = colbuf + (size_t)(act ? col : 0) * CS;
-    float2 v[C::R1];
-    if (act) {
-#pragma unroll
-      for (int i = 0; i < C::R1; ++i) v[i] = base[t + i * (C::R2 + 1)];
-      fft_pass1<N, INV>(v, t, tw);
-    }
-    __syncwarp();
-    if (act) {
-#pragma unroll
-      for (int k1 = 0; k1 < C::R1; ++k1) base[k1 * (C::R2 + 1) + t] = v[p1_index<N>(k1)];
-    }
-    __syncwarp();
-    if (act) {
-#pragma unroll
-      for (int d = 0; d < C::D; ++d)
-#pragma unroll
-        for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = base[(t + C::R2 * d) * (C::R2 + 1) + tt];
-      fft_pass2<N, INV>(v);
-    }
-    __syncwarp();
-    if (act) {
-#pragma unroll
-      for (int d = 0; d < C::D; ++d)
-#pragma unroll
-        for (int k2 = 0; k2 < C::R2; ++k2) {
-          const int yy = t + C::R2 * d + C::R1 * k2;
-          base[yy + yy / C::R2] = v[p2_index<N>(d, k2)];
-        }
-    }
-    __syncwarp();
-  }
-}
-
-struct Pipe {          // per-CTA bookkeeping of the shared-memory barriers
-  uint32_t issued[2];  // TMA loads issued on barrier b (one per strip buffer)
-  uint32_t done[2];    // TMA loads waited for
+struct Pipe {                     // per-CTA bookkeeping of the shared-memory barriers
+  uint32_t issued[kMaxStripBufs];  // TMA loads issued on barrier b (one per strip buffer)
+  uint32_t done[kMaxStripBufs];    // TMA loads waited for
 };
 
 __device__ __forceinline__ void pipe_wait(Pipe& p, uint64_t* bars, int b, int* status) {
@@ -256,6 +212,35 @@ __device__ __forceinline__ void strip_dft(float2* sb, int M, const float2* tw) {
   }
 }
 
+// Modulus projection of one strip, fused with the step to U (see the header):
+// for every pixel of the strip, S = sum_k |X_k|^2, the scale s = sqrt(I) /
+// (N sqrt(S)) (0 where S = 0) and X_k <- (beta s - 1/N^2) X_k; returns this
+// thread's Fourier-error terms added to `ef`.  MM >= M bounds the unrolled
+// mode loops so that the loads of all modes are in flight together.
+template <int N, int MM>
+__device__ __forceinline__ float modulus_strip(float2* sb, const float* ib, int M, float beta, float ef) {
+  constexpr int SW = kStripW;
+  const float invN = 1.f / (float)N;
+  const float invN2 = invN * invN;
+  for (int pq = threadIdx.x; pq < N * SW; pq += kThreads) {
+    const int y = pq / SW, c = pq % SW;   // ib is [column][row]
+    float S = 0.f;
+#pragma unroll
+    for (int k = 0; k < MM; ++k)
+      if (k < M) S += cnorm(sb[k * N * SW + pq]);
+    const float si_ = sqrtf(ib[c * N + y]);
+    const float ss = sqrtf(S);
+    const float sc = (S > 0.f) ? (si_ / ss) * invN : 0.f;
+    const float dd = fmaf(ss, invN, -si_);
+    ef = fmaf(dd, dd, ef);
+    const float f = fmaf(beta, sc, -invN2);
+#pragma unroll
+    for (int k = 0; k < MM; ++k)
+      if (k < M) sb[k * N * SW + pq] = cscale(sb[k * N * SW + pq], f);
+  }
+  return ef;
+}
+
 template <int N>
 __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtensorMap* tmap, float2* sbuf,
                                               float* ibuf, const float2* tw, uint64_t* bars, Pipe& pp, int j,
@@ -263,10 +248,12 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
   constexpr int SW = kStripW;
   const int M = a.M;
   const int tid = threadIdx.x;
-  const float invN = 1.f / (float)N;
-  const float invN2 = invN * invN;
   const float beta = a.beta;
   const int nbuf = a.strip_bufs;
+  // strips loaded ahead of the one being transformed; with three buffers the
+  // buffer a new load goes to was stored from one strip earlier, so its
+  // store has had a whole strip's time to drain
+  const int ahead = nbuf < 2 ? nbuf : 2;
   const uint32_t strip_elems = (uint32_t)M * N * SW;
   const uint32_t strip_bytes = strip_elems * (uint32_t)sizeof(float2);
   float ef = 0.f;  // this thread's few terms; the cross-thread sums are FP64
@@ -284,7 +271,7 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
   };
   if (tid == 0) fence_proxy_async_global();
   issue(0);
-  if (nbuf > 1 && a.SPG > 1) issue(1);
+  if (ahead > 1 && a.SPG > 1) issue(1);
   for (int si = 0; si < a.SPG; ++si) {
     const int s = sg * a.SPG + si;
     const int b = si % nbuf;
@@ -294,24 +281,13 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
     else pp.done[b]++;
     __syncthreads();
     strip_dft<N, false>(sb, M, tw);
-    if (nbuf > 1 && si + 1 < a.SPG) cp_async_wait<1>(); else cp_async_wait<0>();
+    if (ahead > 1 && si + 1 < a.SPG) cp_async_wait<1>(); else cp_async_wait<0>();
     __syncthreads();
-    // modulus projection fused with the step to U (see the header)
-    for (int pq = tid; pq < N * SW; pq += kThreads) {
-      const int y = pq / SW, c = pq % SW;   // ibuf is [column][row]
-      float S = 0.f;
-      for (int k = 0; k < M; ++k) S += cnorm(sb[k * N * SW + pq]);
-      const float si_ = sqrtf(ib[c * N + y]);
-      const float ss = sqrtf(S);
-      const float sc = (S > 0.f) ? (si_ / ss) * invN : 0.f;
-      const float dd = fmaf(ss, invN, -si_);
-      ef = fmaf(dd, dd, ef);
-      const float f = fmaf(beta, sc, -invN2);
-      for (int k = 0; k < M; ++k) {
-        float2& z = sb[k * N * SW + pq];
-        z = cscale(z, f);
-      }
-    }
+    if (M <= 1) ef = modulus_strip<N, 1>(sb, ib, M, beta, ef);
+    else if (M <= 2) ef = modulus_strip<N, 2>(sb, ib, M, beta, ef);
+    else if (M <= 4) ef = modulus_strip<N, 4>(sb, ib, M, beta, ef);
+    else if (M <= 8) ef = modulus_strip<N, 8>(sb, ib, M, beta, ef);
+    else ef = modulus_strip<N, kMaxModes>(sb, ib, M, beta, ef);
     __syncthreads();
     strip_dft<N, true>(sb, M, tw);
     fence_proxy_async_smem();
@@ -320,9 +296,14 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
       tma_store_3d(tmap, s * SW, 0, zview, sb);
       bulk_commit();
     }
-    const int nxt = si + nbuf;
+    const int nxt = si + ahead;
     if (nxt < a.SPG) {
-      if (tid == 0) bulk_wait_read<0>();  // the store has left buffer b
+      // the buffer of strip nxt last held strip nxt - nbuf: wait until its
+      // store has left shared memory
+      if (tid == 0) {
+        if (nbuf > ahead) bulk_wait_read<1>();
+        else bulk_wait_read<0>();
+      }
       __syncthreads();
       issue(nxt);
     }
@@ -345,17 +326,16 @@ __global__ void __launch_bounds__(kThreads, 2)
   float2* stage = work + C::GR * C::XB;
   float2* sbuf = work;
   float* ibuf = reinterpret_cast<float*>(work + (size_t)a.strip_bufs * a.M * N * kStripW);
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[kMaxStripBufs];
   __shared__ int s_task;
   __shared__ int s_skip;
   __shared__ double s_red[kThreads / 32];
   for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
   if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int b = 0; b < kMaxStripBufs; ++b) mbar_init(&bars[b], 1);
     fence_mbar_init();
   }
-  Pipe pp = {{0, 0}, {0, 0}};
+  Pipe pp = {};
 
   int* disp = a.counters;
   int* doneR = a.counters + 1;
@@ -363,6 +343,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   int* doneI = doneC + a.nchunks;
   int next = 0;
   if (threadIdx.x == 0) next = atomicAdd(disp, 1);
+  int st_prev = 0;
   const size_t slot_elems = (size_t)a.B * a.M * N * N;
 
   for (;;) {
@@ -374,13 +355,22 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int task = s_task;
     if (task >= a.total_tasks) break;
 
-    // Decode (stage, kind, chunk, local index).
-    int lo = 0, hi = a.nstages;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (__ldg(a.stage_off + mid) <= task) lo = mid; else hi = mid;
+    // Decode (stage, kind, chunk, local index).  A CTA's tasks increase, so
+    // the stage is the previous one or a later one: look at the next stage
+    // before falling back to a binary search.
+    int lo = st_prev;
+    if (__ldg(a.stage_off + lo + 1) <= task) {
+      ++lo;
+      if (__ldg(a.stage_off + lo + 1) <= task) {
+        int hi = a.nstages;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (__ldg(a.stage_off + mid) <= task) lo = mid; else hi = mid;
+        }
+      }
     }
     const int st = lo;
+    st_prev = lo;
     int local = task - __ldg(a.stage_off + st);
     int kind = -1, c = 0;
     if (st < a.nchunks) {
@@ -447,7 +437,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   // Copies that a timed-out wait left in flight must land before the CTA exits.
   if (threadIdx.x == 0) {
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < kMaxStripBufs; ++b)
       while (pp.done[b] < pp.issued[b]) pipe_wait(pp, bars, b, a.status);
     bulk_wait<0>();
   }

@@ -19,6 +19,7 @@ constexpr int kThreads = 256;          // threads per CTA of every hot kernel
 constexpr int kMetricsRing = 1024;     // iterations of metrics kept on the device
 constexpr int kMaxModes = 16;
 constexpr int kStripW = 2;             // columns per Fourier column strip
+constexpr int kMaxStripBufs = 3;       // strip buffers of a column task
 constexpr int kTwBytes = 2048;         // shared twiddle table (N <= 256 complex values)
 
 // ---------------------------------------------------------------------------
@@ -51,7 +52,7 @@ struct FourierArgs {
   int SPG;                // strips per column task
   int w, lw;              // strip width (columns, = kStripW) and its log2
   int NS;                 // strips per view = N / w
-  int strip_bufs;         // strip buffers of a column task (1 or 2)
+  int strip_bufs;         // strip buffers of a column task (1 to kMaxStripBufs)
   int nstages, total_tasks;
   const int* stage_off;   // [nstages + 1] first task of each stage
   int* counters;          // [0] dispenser, then done R/C/I per chunk
@@ -92,8 +93,8 @@ struct ObjFinalArgs {
 // Probe update (Eq. 4): per-view-group partial sums, then a fixed-order
 // FP64 reduction over the groups and the division.
 // ---------------------------------------------------------------------------
-constexpr int kProbePxPerThread = 2;
-constexpr int kProbePxPerCta = kThreads * kProbePxPerThread;
+constexpr int kProbePxPerThread = 2;   // pixels per thread for M <= 8 (1 above)
+constexpr int kProbeStages = 4;        // depth of the views' shared-memory ring
 
 struct ProbePartialArgs {
   int N, M, J, H, W, groups;
@@ -102,6 +103,7 @@ struct ProbePartialArgs {
   const int2* pos;
   float2* part_num;        // [groups][M][N*N]
   double* part_den;        // [groups][N*N]
+  int* status;             // kStatusTimeout if a ring wait expired
 };
 
 struct ProbeFinalArgs {
@@ -128,7 +130,11 @@ cudaError_t launch_obj_gather(const void* tmap, const ObjGatherArgs& a, int ntil
 cudaError_t launch_obj_final(const ObjFinalArgs& a, int blocks, cudaStream_t s);
 cudaError_t launch_obj_source(float2* cview, const float2* psi, const float2* probe, int N, int M,
                               int J, cudaStream_t s);
-cudaError_t launch_probe_partial(const ProbePartialArgs& a, cudaStream_t s);
+// Pixels per probe tile and the probe-partial kernel's dynamic shared memory.
+int probe_tile_px(int M);
+size_t probe_partial_smem_bytes(int M);
+// Probe partial sums; a persistent grid of min(items, num_sms) CTAs.
+cudaError_t launch_probe_partial(const ProbePartialArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_probe_final(const ProbeFinalArgs& a, cudaStream_t s, int* blocks_out);
 
 cudaError_t launch_init_psi(float2* psi, const float2* probe, const float2* obj, const int2* pos,

@@ -20,12 +20,16 @@
 //    example on two streams without ordering) race on it and give wrong
 //    results; order them on one stream.
 //  * The array keeps the last call's contents; everything a call needs to
-//    start at zero is cleared by the call itself.
+//    start at zero is cleared by the call itself.  Its first word is a status
+//    word: a bounded device wait that expired during a call (which leaves
+//    that call's result wrong rather than hanging the GPU) is reported as
+//    DM_ETIMEOUT by the next call on the same stream, which clears it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <numeric>
 #include <string>
 
 #include "dm.h"
@@ -73,7 +77,8 @@ extern "C" int dm_probe_update_static(const float* psi, const float* object, con
   const size_t nn = (size_t)n * n;
   const int probe_blocks = (int)std::min<size_t>(256, (nn + dmk::kThreads - 1) / dmk::kThreads);
   // fixed part of the layout, then as many view groups as fit
-  const size_t fixed = align256(2 * (size_t)modes * nn * sizeof(double))        // numerator sums
+  const size_t fixed = align256(sizeof(int))                                     // status word
+                       + align256(2 * (size_t)modes * nn * sizeof(double))      // numerator sums
                        + align256(nn * sizeof(double))                           // denominator sums
                        + align256(nn * sizeof(float))                            // sum_k |P_k|^2
                        + align256((size_t)probe_blocks * 2 * modes * sizeof(double))
@@ -102,12 +107,14 @@ extern "C" int dm_probe_update_static(const float* psi, const float* object, con
 
   int num_sms = 0;
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-  const int utiles = (int)((nn + dmk::kProbePxPerCta - 1) / dmk::kProbePxPerCta);
+  if (num_sms < 1) num_sms = 1;
+  const int tiles = (int)((nn + dmk::probe_tile_px(modes) - 1) / dmk::probe_tile_px(modes));
   int groups = (int)((kStaticScratchBytes - fixed) / per_group);
-  groups = std::max(1, std::min(groups, std::min(views, std::max(1, (4 * num_sms + utiles - 1) / utiles))));
+  groups = std::max(1, std::min(groups, std::min(views, num_sms / std::gcd(tiles, num_sms))));
 
   size_t off = 0;
   auto carve = [&](size_t bytes) { unsigned char* p = base + off; off += align256(bytes); return p; };
+  int* status = reinterpret_cast<int*>(carve(sizeof(int)));
   double* num_sum = reinterpret_cast<double*>(carve(2 * (size_t)modes * nn * sizeof(double)));
   double* den_sum = reinterpret_cast<double*>(carve(nn * sizeof(double)));
   float* p2 = reinterpret_cast<float*>(carve(nn * sizeof(float)));
@@ -127,6 +134,14 @@ extern "C" int dm_probe_update_static(const float* psi, const float* object, con
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return fail(DM_ECUDA, cudaGetErrorString(e));
   if (hbad) return fail(DM_EINVAL, "a footprint lies outside the object");
+  int hstatus = 0;
+  if ((e = cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return fail(DM_ECUDA, cudaGetErrorString(e));
+  if (hstatus & dmk::kStatusTimeout) {
+    cudaMemsetAsync(status, 0, sizeof(int), s);
+    return fail(DM_ETIMEOUT, "a bounded device wait of the previous call expired; its result is not valid");
+  }
 
   dmk::ProbePartialArgs a{};
   a.N = n; a.M = modes; a.J = views; a.H = obj_h; a.W = obj_w; a.groups = groups;
@@ -135,7 +150,8 @@ extern "C" int dm_probe_update_static(const float* psi, const float* object, con
   a.pos = pos;
   a.part_num = part_num;
   a.part_den = part_den;
-  if ((e = dmk::launch_probe_partial(a, s)) != cudaSuccess) return fail(DM_ECUDA, cudaGetErrorString(e));
+  a.status = status;
+  if ((e = dmk::launch_probe_partial(a, num_sms, s)) != cudaSuccess) return fail(DM_ECUDA, cudaGetErrorString(e));
   if ((e = cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s)) != cudaSuccess)
     return fail(DM_ECUDA, cudaGetErrorString(e));
   dmk::ProbeFinalArgs f{};

@@ -3,6 +3,8 @@
 // the probe update (Eq. 4) as a two-stage deterministic reduction over views.
 // Also the small kernels around them: initial exit waves (Sec. II), the
 // intensity layout, sum_k |P_k|^2, and the Eq. 6 / Fourier-error reductions.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -181,59 +183,123 @@ __global__ void __launch_bounds__(kThreads) k_obj_source(float2* cview, const fl
 }
 
 // ---------------------------------------------------------------------------
-// Probe update, part 1 (Eq. 4): CTA (pixel tile, view group) sums over its
-// views, for 2 pixels per thread and all modes:
+// Probe update, part 1 (Eq. 4 numerator and denominator partial sums).
+// Work items are (pixel tile, view group); each thread owns PX pixels of the
+// tile and sums over the group's views
 //   num_k(u) += conj(O(r_j + u)) psi_j^k(u),   den(u) += |O(r_j + u)|^2
-// (num in FP32, den in FP32 over 32 views then FP64), and writes partials.
+// (num in FP32, den in FP32 over 32 views then FP64), then writes the item's
+// partials.  A persistent CTA per SM streams the views through a
+// kProbeStages-deep shared-memory ring: one bulk asynchronous copy per mode
+// brings the tile of psi_j^k (contiguous in memory), and each thread copies
+// the object values of its own pixels with 8-byte asynchronous copies, so
+// several views' reads are in flight while one is summed.
 // ---------------------------------------------------------------------------
-template <int MAXM>
-__global__ void __launch_bounds__(kThreads) k_probe_partial(const ProbePartialArgs a) {
+template <int MAXM, int PX>
+__global__ void __launch_bounds__(kThreads, 1) k_probe_partial(const ProbePartialArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[kProbeStages];
+  constexpr int TP = PX * kThreads;  // pixels per tile
   const int N = a.N, M = a.M;
   const int nn = N * N;
-  const int g = blockIdx.y;
-  const int j0 = (int)(((long long)g * a.J) / a.groups);
-  const int j1 = (int)(((long long)(g + 1) * a.J) / a.groups);
-  int u[kProbePxPerThread], uy[kProbePxPerThread], ux[kProbePxPerThread];
-  bool ok[kProbePxPerThread];
-  float2 acc[kProbePxPerThread][MAXM];
-  float den32[kProbePxPerThread];
-  double den64[kProbePxPerThread];
-#pragma unroll
-  for (int q = 0; q < kProbePxPerThread; ++q) {
-    u[q] = blockIdx.x * kProbePxPerCta + q * kThreads + threadIdx.x;
-    ok[q] = u[q] < nn;
-    uy[q] = u[q] / N;
-    ux[q] = u[q] % N;
-    den32[q] = 0.f;
-    den64[q] = 0.0;
-#pragma unroll
-    for (int k = 0; k < MAXM; ++k) acc[q][k] = make_float2(0.f, 0.f);
+  const int tiles = (nn + TP - 1) / TP;
+  const int items = tiles * a.groups;
+  float2* ring = reinterpret_cast<float2*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+  const int stage_elems = (M + 1) * TP;  // M tiles of psi, then the object values
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < kProbeStages; ++b) mbar_init(&full[b], 1);
+    fence_mbar_init();
   }
-  for (int j = j0; j < j1; ++j) {
-    const int2 p = __ldg(a.pos + j);
+  __syncthreads();
+  uint32_t issued = 0, consumed = 0;  // views issued to / taken from the ring by this CTA
+
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int tile = item % tiles, g = item / tiles;
+    const int j0 = (int)(((long long)g * a.J) / a.groups);
+    const int j1 = (int)(((long long)(g + 1) * a.J) / a.groups);
+    const int nv = j1 - j0;
+    const int u0 = tile * TP;
+    const int npx = min(TP, nn - u0);               // a multiple of 256 (nn is)
+    const uint32_t mode_bytes = (uint32_t)npx * sizeof(float2);
+    int uy[PX], ux[PX];
+    bool ok[PX];
+    float2 acc[PX][MAXM];
+    float den32[PX];
+    double den64[PX];
 #pragma unroll
-    for (int q = 0; q < kProbePxPerThread; ++q) {
+    for (int q = 0; q < PX; ++q) {
+      const int u = u0 + q * kThreads + threadIdx.x;
+      ok[q] = q * kThreads + (int)threadIdx.x < npx;
+      uy[q] = u / N;
+      ux[q] = u % N;
+      den32[q] = 0.f;
+      den64[q] = 0.0;
+#pragma unroll
+      for (int k = 0; k < MAXM; ++k) acc[q][k] = make_float2(0.f, 0.f);
+    }
+    // view i of the item into the next ring stage (every thread calls this)
+    auto issue = [&](int i, int2 p) {
+      float2* st = ring + (size_t)(issued % kProbeStages) * stage_elems;
+      if (threadIdx.x == 0) {
+        uint64_t* bar = &full[issued % kProbeStages];
+        mbar_arrive_expect_tx(bar, mode_bytes * (uint32_t)M);
+        const float2* src = a.psi + (size_t)(j0 + i) * M * nn + u0;
+        for (int k = 0; k < M; ++k) bulk_load(st + k * TP, src + (size_t)k * nn, mode_bytes, bar);
+      }
+#pragma unroll
+      for (int q = 0; q < PX; ++q)
+        if (ok[q]) cp_async8(st + M * TP + q * kThreads + threadIdx.x,
+                             a.obj + (size_t)(p.x + uy[q]) * a.W + p.y + ux[q]);
+      ++issued;
+    };
+    // prologue: kProbeStages - 1 views in flight (one commit group each)
+    for (int i = 0; i < kProbeStages - 1; ++i) {
+      if (i < nv) issue(i, __ldg(a.pos + j0 + i));
+      cp_async_commit();
+    }
+    int2 p_next = (kProbeStages - 1 < nv) ? __ldg(a.pos + j0 + kProbeStages - 1) : make_int2(0, 0);
+    for (int v = 0; v < nv; ++v) {
+      const int b = consumed % kProbeStages;
+      if (threadIdx.x == 0) mbar_wait_bounded(&full[b], (consumed / kProbeStages) & 1u, a.status);
+      cp_async_wait<kProbeStages - 2>();
+      __syncthreads();
+      // the stage consumed in the previous step is free for view v + S - 1
+      if (v + kProbeStages - 1 < nv) issue(v + kProbeStages - 1, p_next);
+      cp_async_commit();
+      if (v + kProbeStages < nv) p_next = __ldg(a.pos + j0 + v + kProbeStages);
+      const float2* st = ring + (size_t)b * stage_elems;
+#pragma unroll
+      for (int q = 0; q < PX; ++q) {
+        if (!ok[q]) continue;
+        const float2 o = st[M * TP + q * kThreads + threadIdx.x];
+        den32[q] = fmaf(o.x, o.x, fmaf(o.y, o.y, den32[q]));
+#pragma unroll
+        for (int k = 0; k < MAXM; ++k)
+          if (k < M) acc[q][k] = cadd(acc[q][k], cconjmul(o, st[k * TP + q * kThreads + threadIdx.x]));
+      }
+      ++consumed;
+      if ((v & 31) == 31) {
+#pragma unroll
+        for (int q = 0; q < PX; ++q) { den64[q] += den32[q]; den32[q] = 0.f; }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PX; ++q) {
       if (!ok[q]) continue;
-      const float2 o = __ldg(a.obj + (size_t)(p.x + uy[q]) * a.W + p.y + ux[q]);
-      den32[q] = fmaf(o.x, o.x, fmaf(o.y, o.y, den32[q]));
-      const float2* ps = a.psi + (size_t)j * M * nn + u[q];
+      const int u = u0 + q * kThreads + threadIdx.x;
+      a.part_den[(size_t)g * nn + u] = den64[q] + den32[q];
 #pragma unroll
       for (int k = 0; k < MAXM; ++k)
-        if (k < M) acc[q][k] = cadd(acc[q][k], cconjmul(o, __ldcs(ps + (size_t)k * nn)));
+        if (k < M) a.part_num[((size_t)g * M + k) * nn + u] = acc[q][k];
     }
-    if (((j - j0) & 31) == 31) {
-#pragma unroll
-      for (int q = 0; q < kProbePxPerThread; ++q) { den64[q] += den32[q]; den32[q] = 0.f; }
+    __syncthreads();  // every thread is done with the ring before the next item refills it
+  }
+  // copies that a timed-out wait left in flight land before the CTA exits
+  if (threadIdx.x == 0)
+    while (consumed < issued) {
+      mbar_wait_bounded(&full[consumed % kProbeStages], (consumed / kProbeStages) & 1u, a.status);
+      ++consumed;
     }
-  }
-#pragma unroll
-  for (int q = 0; q < kProbePxPerThread; ++q) {
-    if (!ok[q]) continue;
-    a.part_den[(size_t)g * nn + u[q]] = den64[q] + den32[q];
-#pragma unroll
-    for (int k = 0; k < MAXM; ++k)
-      if (k < M) a.part_num[((size_t)g * M + k) * nn + u[q]] = acc[q][k];
-  }
+  cp_async_wait<0>();
 }
 
 // Probe update, part 2a: FP64 sums over the view groups, in group order.
@@ -440,15 +506,30 @@ cudaError_t launch_obj_source(float2* cview, const float2* psi, const float2* pr
   return cudaGetLastError();
 }
 
-cudaError_t launch_probe_partial(const ProbePartialArgs& a, cudaStream_t s) {
-  const int nn = a.N * a.N;
-  dim3 grid((nn + kProbePxPerCta - 1) / kProbePxPerCta, a.groups);
-  if (a.M <= 1) k_probe_partial<1><<<grid, kThreads, 0, s>>>(a);
-  else if (a.M <= 2) k_probe_partial<2><<<grid, kThreads, 0, s>>>(a);
-  else if (a.M <= 4) k_probe_partial<4><<<grid, kThreads, 0, s>>>(a);
-  else if (a.M <= 8) k_probe_partial<8><<<grid, kThreads, 0, s>>>(a);
-  else k_probe_partial<16><<<grid, kThreads, 0, s>>>(a);
+template <int MAXM, int PX>
+static cudaError_t probe_partial_launch(const ProbePartialArgs& a, int num_sms, cudaStream_t s) {
+  const size_t smem = probe_partial_smem_bytes(a.M);
+  const void* f = (const void*)k_probe_partial<MAXM, PX>;
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int tp = PX * kThreads;
+  const int items = ((a.N * a.N + tp - 1) / tp) * a.groups;
+  k_probe_partial<MAXM, PX><<<std::min(items, num_sms), kThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+int probe_tile_px(int M) { return (M > 8 ? 1 : kProbePxPerThread) * kThreads; }
+
+size_t probe_partial_smem_bytes(int M) {
+  return 128 + (size_t)kProbeStages * (M + 1) * probe_tile_px(M) * sizeof(float2);
+}
+
+cudaError_t launch_probe_partial(const ProbePartialArgs& a, int num_sms, cudaStream_t s) {
+  if (a.M <= 1) return probe_partial_launch<1, kProbePxPerThread>(a, num_sms, s);
+  if (a.M <= 2) return probe_partial_launch<2, kProbePxPerThread>(a, num_sms, s);
+  if (a.M <= 4) return probe_partial_launch<4, kProbePxPerThread>(a, num_sms, s);
+  if (a.M <= 8) return probe_partial_launch<8, kProbePxPerThread>(a, num_sms, s);
+  return probe_partial_launch<16, 1>(a, num_sms, s);
 }
 
 // Runs 2a and 2b; *blocks_out receives the number of partial rows of 2b.
