@@ -539,7 +539,8 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   DM_TRY(alloc_n(c, &c->obj[1], (size_t)c->H * c->W));
   DM_TRY(alloc_n(c, &c->p2, nn));
   DM_TRY(alloc_n(c, &c->pos, (size_t)J));
-  DM_TRY(alloc_n(c, &c->tw, (size_t)N));
+  const int ntw = dmk::fourier_twiddles(N, nullptr);
+  DM_TRY(alloc_n(c, &c->tw, (size_t)ntw));
   DM_TRY(alloc_n(c, &c->status, 1));
   DM_TRY(alloc_n(c, &c->isum, 1));
   DM_TRY(alloc_n(c, &c->ring, (size_t)dmk::kMetricsRing * (2 + dmk::kMaxModes)));
@@ -549,12 +550,9 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
     cuda_fail(c, e, "memset"); return bail(DM_ECUDA);
   }
 
-  std::vector<float2> htw(N);
-  for (int m = 0; m < N; ++m) {
-    const double a = -2.0 * M_PI * (double)m / (double)N;
-    htw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
-  DM_TRY(copy_in(c, c->tw, htw.data(), N * sizeof(float2), DM_HOST));
+  std::vector<float2> htw(ntw);
+  dmk::fourier_twiddles(N, htw.data());
+  DM_TRY(copy_in(c, c->tw, htw.data(), ntw * sizeof(float2), DM_HOST));
   DM_TRY(copy_in(c, c->pos, hpos.data(), hpos.size() * sizeof(int32_t), DM_HOST));
   DM_TRY(copy_in(c, c->probe[0], probe0, (size_t)M * nn * sizeof(float2), p->mem_kind));
   DM_TRY(copy_in(c, c->obj[0], object0, (size_t)c->H * c->W * sizeof(float2), p->mem_kind));

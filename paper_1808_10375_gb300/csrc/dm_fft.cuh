@@ -3,7 +3,7 @@
 // A length-N transform (N = R1 * R2, a power of two) is computed by a group
 // of R2 threads that each hold R1 complex values:
 //   pass 1: thread t transforms x[t + R2*i], i < R1, in registers (an R1-point
-//           DFT), then multiplies output k1 by W_N^(t*k1);
+//           DFT), then multiplies output k1 by W_N^(t*k1) (table twF, below);
 //   exchange through a small shared buffer laid out [k1][t ^ (k1 mod R2)]
 //           (the XOR swizzle keeps both access patterns bank-conflict free);
 //   pass 2: thread t' transforms, for each k1 = t' + R2*d (d < R1/R2), the R2
@@ -169,18 +169,41 @@ template <> struct FftShape<64>  { static constexpr int R1 = 8,  R2 = 8;  };
 template <> struct FftShape<128> { static constexpr int R1 = 16, R2 = 8;  };
 template <> struct FftShape<256> { static constexpr int R1 = 16, R2 = 16; };
 
+// Twiddle tables, both holding W_N^(t k1) = exp(-2 pi i t k1 / N):
+//   twF[k1 * R2 + t] (k1 < R1, t < R2): pass 1, where thread t reads one row
+//       per k1 (consecutive threads, consecutive entries);
+//   twD[t * R1 + k1]: the inverse that starts from the pass-2 distribution
+//       (below), where the thread holding k1 reads one entry per t.
+// When R1 == R2 the two tables coincide (W is symmetric in t and k1) and only
+// twF is stored; otherwise twD follows twF.  tw_entries<N>() is the total.
+template <int N>
+DM_HD constexpr int tw_entries() { return FftShape<N>::R1 == FftShape<N>::R2 ? N : 2 * N; }
+
+template <int N>
+DM_HD const float2* tw_dif(const float2* twF) { return FftShape<N>::R1 == FftShape<N>::R2 ? twF : twF + N; }
+
+// Host side: fill the tables from w(m) = W_N^m (computed in double precision).
+template <int N, class F>
+inline void tw_fill(float2* tab, F w) {
+  constexpr int R1 = FftShape<N>::R1, R2 = FftShape<N>::R2;
+  for (int k1 = 0; k1 < R1; ++k1)
+    for (int t = 0; t < R2; ++t) tab[k1 * R2 + t] = w((t * k1) % N);
+  if (R1 != R2)
+    for (int t = 0; t < R2; ++t)
+      for (int k1 = 0; k1 < R1; ++k1) tab[N + t * R1 + k1] = w((t * k1) % N);
+}
+
 // Pass 1 for thread t, in place: v[i] = x[t + R2 i] on entry; on return the
 // twiddled value for k1, Y_t[k1] W_N^(t k1), sits at v[p1_index(k1)].
-// tw[m] = exp(-2 pi i m / N).
 template <int N>
 DM_HD constexpr int p1_index(int k1) { return out_index<FftShape<N>::R1>(k1); }
 
 template <int N, bool INV>
-DM_HD void fft_pass1(float2 (&v)[FftShape<N>::R1], int t, const float2* tw) {
-  constexpr int R1 = FftShape<N>::R1;
+DM_HD void fft_pass1(float2 (&v)[FftShape<N>::R1], int t, const float2* twF) {
+  constexpr int R1 = FftShape<N>::R1, R2 = FftShape<N>::R2;
   dft_reg<R1, INV>(v);
 #pragma unroll
-  for (int k1 = 1; k1 < R1; ++k1) v[out_index<R1>(k1)] = ctw<INV>(v[out_index<R1>(k1)], tw[t * k1]);
+  for (int k1 = 1; k1 < R1; ++k1) v[out_index<R1>(k1)] = ctw<INV>(v[out_index<R1>(k1)], twF[k1 * R2 + t]);
 }
 
 // Pass 2 for thread t', in place: u[d*R2 + t] = Y_t[k1 = t' + R2 d] on entry
@@ -193,6 +216,36 @@ DM_HD void fft_pass2(float2 (&u)[FftShape<N>::R1]) {
   constexpr int R1 = FftShape<N>::R1, R2 = FftShape<N>::R2, D = R1 / R2;
 #pragma unroll
   for (int d = 0; d < D; ++d) dft_reg<R2, INV>(u + d * R2);
+}
+
+// Inverse transform taken from the pass-2 distribution (no reordering in
+// between): thread t' holds X[k1 + R1 k2], k1 = t' + R2 d, at
+// u[p2_index(d, k2)].  With n = t + R2 i,
+//   x[n] = sum_k1 W_R1^(-i k1) W_N^(-t k1) sum_k2 X[k1 + R1 k2] W_R2^(-t k2),
+// so step A (in registers) is, for each d, an R2-point inverse DFT over k2
+// followed by the factor W_N^(-t k1); afterwards the value for (k1, t) sits
+// at u[d * R2 + t].  After an exchange that gives thread t the values for
+// every k1 (natural order, v[k1]), step B is the R1-point inverse DFT over
+// k1, leaving x[t + R2 i] at v[p1_index(i)]: the distribution pass 1 reads.
+template <int N>
+DM_HD void ifft_stepA(float2 (&u)[FftShape<N>::R1], int tp, const float2* twD) {
+  constexpr int R1 = FftShape<N>::R1, R2 = FftShape<N>::R2, D = R1 / R2;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    float2 w[R2];
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) w[k2] = u[d * R2 + out_index<R2>(k2)];
+    dft_reg<R2, true>(w);
+    const int k1 = tp + R2 * d;
+    u[d * R2] = w[out_index<R2>(0)];
+#pragma unroll
+    for (int t = 1; t < R2; ++t) u[d * R2 + t] = ctw<true>(w[out_index<R2>(t)], twD[t * R1 + k1]);
+  }
+}
+
+template <int N>
+DM_HD void ifft_stepB(float2 (&v)[FftShape<N>::R1]) {
+  dft_reg<FftShape<N>::R1, true>(v);
 }
 
 }  // namespace dmk

@@ -40,11 +40,11 @@ struct FCfg {
 };
 
 // ------------------------------------------------------------------ R task
-// The 16 lanes of a transform stage their row of psi and of P for the next
+// The R2 lanes of a transform stage their row of psi and of P for the next
 // mode with 16-byte asynchronous copies while the current mode is computed;
 // the row buffers belong to the transform, so only warp-level sync is needed.
 template <int N>
-__device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, float2* stage, const float2* tw,
+__device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, float2* stage, const float2* twF,
                                             int j, int jj, int rb, float2* slot) {
   using C = FCfg<N>;
   const int g = threadIdx.x / C::R2, t = threadIdx.x % C::R2;
@@ -78,7 +78,7 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, fl
     }
     __syncwarp();
     if (k + 1 < a.M) issue(k + 1);
-    fft_pass1<N, false>(v, t, tw);
+    fft_pass1<N, false>(v, t, twF);
     __syncwarp();
 #pragma unroll
     for (int k1 = 0; k1 < C::R1; ++k1) xg[k1 * C::R2 + (t ^ (k1 & (C::R2 - 1)))] = v[p1_index<N>(k1)];
@@ -97,8 +97,13 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, fl
 }
 
 // ------------------------------------------------------------------ I task
+// The row of U for the next mode is staged (16-byte asynchronous copies) as
+// soon as the current one is in registers, and the probe row of the next mode
+// once the current epilogue has used its own; the object-source sum over the
+// modes stays in registers (each thread owns the same positions for every
+// mode).  Pending copy groups at the top of mode k: U_k, P_k.
 template <int N>
-__device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, float2* stage, const float2* tw,
+__device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, float2* stage, const float2* twF,
                                             int j, int jj, int rb, const float2* slot) {
   using C = FCfg<N>;
   const int g = threadIdx.x / C::R2, t = threadIdx.x % C::R2;
@@ -107,18 +112,26 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, fl
   const int2 p = a.pos[j];
   const float2* orow = a.obj + (size_t)(p.x + y) * a.W + p.y;
   float2* xg = xb + g * C::XB;
-  // c_j accumulator for this row; each thread owns the positions its pass 2
-  // produces, so no synchronisation is needed.
-  float2* cacc = stage + g * N;
+  float2* urow_s = stage + g * N;              // staged row of U
+  float2* prow_s = stage + (C::GR + g) * N;    // staged probe row
   const float c2b = 2.f - a.beta;
+  auto stage_row = [&](float2* dst, const float2* src) {
+    for (int q = t; q < N / 2; q += C::R2) cp_async16(dst + 2 * q, src + 2 * q);
+    cp_async_commit();
+  };
+  stage_row(urow_s, slot + (((size_t)jj * a.M) * N + y) * N);
+  stage_row(prow_s, a.probe + (size_t)y * N);
+  float2 cacc[C::R1];
   for (int k = 0; k < a.M; ++k) {
-    const float2* prow = a.probe + ((size_t)k * N + y) * N;
-    float2* srow = a.psi + (((size_t)j * a.M + k) * N + y) * N;
-    const float2* urow = slot + (((size_t)jj * a.M + k) * N + y) * N;
+    cp_async_wait<1>();   // U_k
+    __syncwarp();
     float2 v[C::R1];
 #pragma unroll
-    for (int i = 0; i < C::R1; ++i) v[i] = __ldcg(urow + t + C::R2 * i);
-    fft_pass1<N, true>(v, t, tw);
+    for (int i = 0; i < C::R1; ++i) v[i] = urow_s[t + C::R2 * i];
+    __syncwarp();
+    const bool more = k + 1 < a.M;
+    if (more) stage_row(urow_s, slot + (((size_t)jj * a.M + k + 1) * N + y) * N);
+    fft_pass1<N, true>(v, t, twF);
     __syncwarp();
 #pragma unroll
     for (int k1 = 0; k1 < C::R1; ++k1) xg[k1 * C::R2 + (t ^ (k1 & (C::R2 - 1)))] = v[p1_index<N>(k1)];
@@ -128,32 +141,34 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, fl
 #pragma unroll
       for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = xg[(t + C::R2 * d) * C::R2 + (tt ^ t)];
     fft_pass2<N, true>(v);
+    if (more) cp_async_wait<1>(); else cp_async_wait<0>();   // P_k
+    __syncwarp();
+    float2* srow = a.psi + (((size_t)j * a.M + k) * N + y) * N;
 #pragma unroll
     for (int d = 0; d < C::D; ++d) {
 #pragma unroll
       for (int k2 = 0; k2 < C::R2; ++k2) {
         const int x = t + C::R2 * d + C::R1 * k2;
-        const float2 pk = __ldg(prow + x);
+        const float2 pk = prow_s[x];
         const float2 po = cmul(pk, __ldg(orow + x));
         const float2 g2 = v[p2_index<N>(d, k2)];
         const float2 pn = make_float2(fmaf(c2b, po.x, g2.x), fmaf(c2b, po.y, g2.y));
         __stcs(srow + x, pn);
         const float2 cn = cconjmul(pk, pn);
-        cacc[x] = k == 0 ? cn : cadd(cacc[x], cn);
+        cacc[d * C::R2 + k2] = k == 0 ? cn : cadd(cacc[d * C::R2 + k2], cn);
       }
     }
+    __syncwarp();
+    if (more) stage_row(prow_s, a.probe + ((size_t)(k + 1) * N + y) * N);
   }
   float2* crow = a.cview + ((size_t)j * N + y) * N;
 #pragma unroll
   for (int d = 0; d < C::D; ++d)
 #pragma unroll
-    for (int k2 = 0; k2 < C::R2; ++k2) {
-      const int x = t + C::R2 * d + C::R1 * k2;
-      __stcs(crow + x, cacc[x]);
-    }
+    for (int k2 = 0; k2 < C::R2; ++k2) __stcs(crow + t + C::R2 * d + C::R1 * k2, cacc[d * C::R2 + k2]);
 }
 
-struct Pipe {                     // per-CTA bookkeeping of the shared-memory barriers
+struct Pipe {                     // per-thread bookkeeping of the strip barriers
   uint32_t issued[kMaxStripBufs];  // TMA loads issued on barrier b (one per strip buffer)
   uint32_t done[kMaxStripBufs];    // TMA loads waited for
 };
@@ -164,102 +179,169 @@ __device__ __forceinline__ void pipe_wait(Pipe& p, uint64_t* bars, int b, int* s
 }
 
 // ------------------------------------------------------------------ C task
-// Strips of kStripW columns of every mode move between the row-major scratch
-// and shared memory as 3-D TMA boxes (kStripW x N rows x M modes), laid out
-// [mode][row][column] in shared memory.  The task's strips are double-buffered:
-// the next strip's box and intensities load while the current one is
-// transformed, and U goes back with a TMA store.  Column c of mode k is the
-// stride-kStripW sequence at colbuf + k N kStripW + c; its exchange slots
-// follow the in-place XOR pattern of the row transforms.
-template <int N, bool INV>
-__device__ __forceinline__ void strip_dft(float2* sb, int M, const float2* tw) {
-  using C = FCfg<N>;
-  constexpr int SW = kStripW;
-  const int g = threadIdx.x / C::R2, t = threadIdx.x % C::R2;
-  const int ncol = M * SW;
-  for (int col0 = 0; col0 < ncol; col0 += C::GROUPS) {
-    const int col = col0 + g;
-    const bool act = col < ncol;
-    const int k = act ? col / SW : 0, c = col % SW;
-    float2* base = sb + k * N * SW + c;
-    float2 v[C::R1];
-    if (act) {
-#pragma unroll
-      for (int i = 0; i < C::R1; ++i) v[i] = base[(t + C::R2 * i) * SW];
-      fft_pass1<N, INV>(v, t, tw);
-    }
-    __syncwarp();
-    if (act) {
-#pragma unroll
-      for (int k1 = 0; k1 < C::R1; ++k1) base[(k1 * C::R2 + (t ^ (k1 & (C::R2 - 1)))) * SW] = v[p1_index<N>(k1)];
-    }
-    __syncwarp();
-    if (act) {
-#pragma unroll
-      for (int d = 0; d < C::D; ++d)
-#pragma unroll
-        for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = base[((t + C::R2 * d) * C::R2 + (tt ^ t)) * SW];
-      fft_pass2<N, INV>(v);
-    }
-    __syncwarp();
-    if (act) {
-#pragma unroll
-      for (int d = 0; d < C::D; ++d)
-#pragma unroll
-        for (int k2 = 0; k2 < C::R2; ++k2) base[(t + C::R2 * d + C::R1 * k2) * SW] = v[p2_index<N>(d, k2)];
-    }
-    __syncwarp();
-  }
+// Strips of kStripW = 2 columns of every mode move between the row-major
+// scratch and shared memory as 3-D TMA boxes (2 columns x N rows x M modes),
+// laid out [mode][row][column]; the task's strips are double- or triple-
+// buffered and U goes back with a TMA store.
+//
+// Each mode of a strip is transformed by 2 R2 threads ("a slot"), lane bit 0
+// picking the column, so that every half-warp reads and writes whole 16-byte
+// rows of the strip (no bank conflicts in either exchange).  The forward
+// column DFT ends in the pass-2 distribution; the modulus projection is
+// applied there in registers, and the inverse starts from that distribution
+// (ifft_stepA/B), so no reordering exchange sits between the two transforms.
+// The mode sum S(q) = sum_k |X_k(q)|^2 is the only cross-slot step: every slot
+// writes |X_k|^2, one pass computes the factor (beta s - 1/N^2) per pixel, and
+// every slot reads it back.  With more modes than slots (N = 256, M > 8) the
+// slots take the modes in rounds and keep X in their part of the strip.
+template <int N>
+struct CCfg {
+  static constexpr int R1 = FftShape<N>::R1, R2 = FftShape<N>::R2, D = R1 / R2;
+  static constexpr int TPM = kStripW * R2;     // threads per mode slot
+  static constexpr int SLOTS = kThreads / TPM; // modes per round
+};
+static_assert(kStripW == 2, "the column-task lane layout assumes two columns per strip");
+
+template <int N>
+__device__ __forceinline__ unsigned slot_mask() {
+  constexpr int TPM = CCfg<N>::TPM;
+  if constexpr (TPM >= 32) return 0xffffffffu;
+  else return ((1u << TPM) - 1u) << ((threadIdx.x & 31) & ~(TPM - 1));
 }
 
-// Modulus projection of one strip, fused with the step to U (see the header):
-// for every pixel of the strip, S = sum_k |X_k|^2, the scale s = sqrt(I) /
-// (N sqrt(S)) (0 where S = 0) and X_k <- (beta s - 1/N^2) X_k; returns this
-// thread's Fourier-error terms added to `ef`.  MM >= M bounds the unrolled
-// mode loops so that the loads of all modes are in flight together.
-template <int N, int MM>
-__device__ __forceinline__ float modulus_strip(float2* sb, const float* ib, int M, float beta, float ef) {
+// Forward column DFT of the column this thread's slot lane owns; `base`
+// addresses row 0 of that column (row r at base[r * kStripW]).  Returns X in
+// the pass-2 distribution.
+template <int N>
+__device__ __forceinline__ void col_forward(float2* base, int t, const float2* twF, unsigned mask,
+                                            float2 (&v)[FftShape<N>::R1]) {
+  using C = CCfg<N>;
   constexpr int SW = kStripW;
+#pragma unroll
+  for (int i = 0; i < C::R1; ++i) v[i] = base[(t + C::R2 * i) * SW];
+  fft_pass1<N, false>(v, t, twF);
+  __syncwarp(mask);
+#pragma unroll
+  for (int k1 = 0; k1 < C::R1; ++k1) base[(k1 * C::R2 + (t ^ (k1 & (C::R2 - 1)))) * SW] = v[p1_index<N>(k1)];
+  __syncwarp(mask);
+#pragma unroll
+  for (int d = 0; d < C::D; ++d)
+#pragma unroll
+    for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = base[((t + C::R2 * d) * C::R2 + (tt ^ t)) * SW];
+  fft_pass2<N, false>(v);
+}
+
+// Positions a thread owns in its column between the two exchanges (the
+// pass-2 read positions): where X waits when the modes take several rounds.
+template <int N>
+__device__ __forceinline__ int own_row(int t, int r) {
+  using C = CCfg<N>;
+  const int d = r / C::R2, tt = r % C::R2;
+  return (t + C::R2 * d) * C::R2 + (tt ^ t);
+}
+
+// Inverse column DFT from the pass-2 distribution; writes x back to the rows
+// pass 1 read.
+template <int N>
+__device__ __forceinline__ void col_inverse(float2* base, int t, const float2* twD, unsigned mask,
+                                            float2 (&v)[FftShape<N>::R1]) {
+  using C = CCfg<N>;
+  constexpr int SW = kStripW;
+  ifft_stepA<N>(v, t, twD);
+#pragma unroll
+  for (int r = 0; r < C::R1; ++r) base[own_row<N>(t, r) * SW] = v[r];
+  __syncwarp(mask);
+#pragma unroll
+  for (int k1 = 0; k1 < C::R1; ++k1) v[k1] = base[(k1 * C::R2 + (t ^ (k1 & (C::R2 - 1)))) * SW];
+  __syncwarp(mask);
+  ifft_stepB<N>(v);
+#pragma unroll
+  for (int i = 0; i < C::R1; ++i) base[(t + C::R2 * i) * SW] = v[p1_index<N>(i)];
+}
+
+// |X|^2 of this thread's pixels into the mode's norm row (layout [q][column]).
+template <int N>
+__device__ __forceinline__ void col_norms(float* nrm, int t, int c, const float2 (&v)[FftShape<N>::R1]) {
+  using C = CCfg<N>;
+#pragma unroll
+  for (int d = 0; d < C::D; ++d)
+#pragma unroll
+    for (int k2 = 0; k2 < C::R2; ++k2) nrm[(t + C::R2 * d + C::R1 * k2) * kStripW + c] = cnorm(v[p2_index<N>(d, k2)]);
+}
+
+template <int N>
+__device__ __forceinline__ void col_scale(const float* fb, int t, int c, float2 (&v)[FftShape<N>::R1]) {
+  using C = CCfg<N>;
+#pragma unroll
+  for (int d = 0; d < C::D; ++d)
+#pragma unroll
+    for (int k2 = 0; k2 < C::R2; ++k2) {
+      const int q = t + C::R2 * d + C::R1 * k2;
+      v[p2_index<N>(d, k2)] = cscale(v[p2_index<N>(d, k2)], fb[q * kStripW + c]);
+    }
+}
+
+// Modulus factor per strip pixel p = q * 2 + c: S = sum_k nrm_k[p], the scale
+// s = sqrt(I) / (N sqrt(S)) (0 where S = 0) and f = beta s - 1/N^2 into fb[p];
+// returns this thread's Fourier-error terms added to `ef`.  MM >= M bounds the
+// unrolled mode loop.
+template <int N, int MM>
+__device__ __forceinline__ float col_factor(const float* nrm, int nstride, const float* ib, float* fb, int M,
+                                            float beta, float ef) {
   const float invN = 1.f / (float)N;
   const float invN2 = invN * invN;
-  for (int pq = threadIdx.x; pq < N * SW; pq += kThreads) {
-    const int y = pq / SW, c = pq % SW;   // ib is [column][row]
+  for (int p = threadIdx.x; p < N * kStripW; p += kThreads) {
     float S = 0.f;
 #pragma unroll
     for (int k = 0; k < MM; ++k)
-      if (k < M) S += cnorm(sb[k * N * SW + pq]);
-    const float si_ = sqrtf(ib[c * N + y]);
+      if (k < M) S += nrm[k * nstride + p];
+    const float si_ = sqrtf(ib[p]);
     const float ss = sqrtf(S);
     const float sc = (S > 0.f) ? (si_ / ss) * invN : 0.f;
     const float dd = fmaf(ss, invN, -si_);
     ef = fmaf(dd, dd, ef);
-    const float f = fmaf(beta, sc, -invN2);
-#pragma unroll
-    for (int k = 0; k < MM; ++k)
-      if (k < M) sb[k * N * SW + pq] = cscale(sb[k * N * SW + pq], f);
+    fb[p] = fmaf(beta, sc, -invN2);
   }
   return ef;
 }
 
 template <int N>
+__device__ __forceinline__ float col_factor_any(const float* nrm, int nstride, const float* ib, float* fb, int M,
+                                                float beta, float ef) {
+  if (M <= 1) return col_factor<N, 1>(nrm, nstride, ib, fb, M, beta, ef);
+  if (M <= 2) return col_factor<N, 2>(nrm, nstride, ib, fb, M, beta, ef);
+  if (M <= 4) return col_factor<N, 4>(nrm, nstride, ib, fb, M, beta, ef);
+  if (M <= 8) return col_factor<N, 8>(nrm, nstride, ib, fb, M, beta, ef);
+  return col_factor<N, kMaxModes>(nrm, nstride, ib, fb, M, beta, ef);
+}
+
+template <int N>
 __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtensorMap* tmap, float2* sbuf,
-                                              float* ibuf, const float2* tw, uint64_t* bars, Pipe& pp, int j,
-                                              int zview, int sg) {
+                                              float* ibuf, float* fbuf, float* nbuf, const float2* twF,
+                                              uint64_t* bars, Pipe& pp, int j, int zview, int sg) {
+  using C = CCfg<N>;
   constexpr int SW = kStripW;
   const int M = a.M;
   const int tid = threadIdx.x;
   const float beta = a.beta;
-  const int nbuf = a.strip_bufs;
+  const int nbufs = a.strip_bufs;
+  const float2* twD = tw_dif<N>(twF);
   // strips loaded ahead of the one being transformed; with three buffers the
   // buffer a new load goes to was stored from one strip earlier, so its
   // store has had a whole strip's time to drain
-  const int ahead = nbuf < 2 ? nbuf : 2;
+  const int ahead = nbufs < 2 ? nbufs : 2;
   const uint32_t strip_elems = (uint32_t)M * N * SW;
   const uint32_t strip_bytes = strip_elems * (uint32_t)sizeof(float2);
+  const int slot = tid / C::TPM, c = tid & 1, t = (tid >> 1) & (C::R2 - 1);
+  const unsigned mask = slot_mask<N>();
+  const int rounds = (M + C::SLOTS - 1) / C::SLOTS;
+  // norms: in a single round each slot's part of the strip is free once its
+  // forward transform is done; otherwise in the separate buffer
+  const int nstride = rounds == 1 ? 2 * N * SW : N * SW;   // floats per mode
   float ef = 0.f;  // this thread's few terms; the cross-thread sums are FP64
-  auto issue = [&](int si) {  // strip si of the task into buffer si % nbuf (all threads)
+  auto issue = [&](int si) {  // strip si of the task into buffer si % nbufs (all threads)
     const int s = sg * a.SPG + si;
-    const int b = si % nbuf;
+    const int b = si % nbufs;
     if (tid == 0) {
       mbar_arrive_expect_tx(&bars[b], strip_bytes);
       tma_load_3d(sbuf + (size_t)b * strip_elems, tmap, s * SW, 0, zview, &bars[b]);
@@ -274,37 +356,67 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
   if (ahead > 1 && a.SPG > 1) issue(1);
   for (int si = 0; si < a.SPG; ++si) {
     const int s = sg * a.SPG + si;
-    const int b = si % nbuf;
+    const int b = si % nbufs;
     float2* sb = sbuf + (size_t)b * strip_elems;
     const float* ib = ibuf + b * (N * SW);
-    if (tid == 0) pipe_wait(pp, bars, b, a.status);
-    else pp.done[b]++;
-    __syncthreads();
-    strip_dft<N, false>(sb, M, tw);
+    pipe_wait(pp, bars, b, a.status);   // every thread waits for the strip itself
+    float* nrm = rounds == 1 ? reinterpret_cast<float*>(sb) : nbuf;
+    float2 v[C::R1];
+    if (rounds == 1) {
+      if (slot < M) {
+        float2* base = sb + slot * N * SW + c;
+        col_forward<N>(base, t, twF, mask, v);
+        __syncwarp(mask);   // the slot's exchange reads are done: its part holds the norms now
+        col_norms<N>(nrm + slot * nstride, t, c, v);
+      }
+    } else {
+      for (int r = 0; r < rounds; ++r) {
+        const int k = r * C::SLOTS + slot;
+        if (k < M) {
+          float2* base = sb + k * N * SW + c;
+          col_forward<N>(base, t, twF, mask, v);
+          col_norms<N>(nrm + k * nstride, t, c, v);
+#pragma unroll
+          for (int q = 0; q < C::R1; ++q) base[own_row<N>(t, q) * SW] = v[q];
+        }
+      }
+    }
     if (ahead > 1 && si + 1 < a.SPG) cp_async_wait<1>(); else cp_async_wait<0>();
-    __syncthreads();
-    if (M <= 1) ef = modulus_strip<N, 1>(sb, ib, M, beta, ef);
-    else if (M <= 2) ef = modulus_strip<N, 2>(sb, ib, M, beta, ef);
-    else if (M <= 4) ef = modulus_strip<N, 4>(sb, ib, M, beta, ef);
-    else if (M <= 8) ef = modulus_strip<N, 8>(sb, ib, M, beta, ef);
-    else ef = modulus_strip<N, kMaxModes>(sb, ib, M, beta, ef);
-    __syncthreads();
-    strip_dft<N, true>(sb, M, tw);
+    __syncthreads();   // A: every mode's norms (and this strip's intensities) are in place
+    ef = col_factor_any<N>(nrm, nstride, ib, fbuf, M, beta, ef);
+    __syncthreads();   // B: the factors are in place; the norms are no longer read
+    if (rounds == 1) {
+      if (slot < M) {
+        col_scale<N>(fbuf, t, c, v);
+        col_inverse<N>(sb + slot * N * SW + c, t, twD, mask, v);
+      }
+    } else {
+      for (int r = 0; r < rounds; ++r) {
+        const int k = r * C::SLOTS + slot;
+        if (k < M) {
+          float2* base = sb + k * N * SW + c;
+#pragma unroll
+          for (int q = 0; q < C::R1; ++q) v[q] = base[own_row<N>(t, q) * SW];
+          col_scale<N>(fbuf, t, c, v);
+          col_inverse<N>(base, t, twD, mask, v);
+        }
+      }
+    }
     fence_proxy_async_smem();
-    __syncthreads();
+    __syncthreads();   // C: U of every mode is in the strip
     if (tid == 0) {
       tma_store_3d(tmap, s * SW, 0, zview, sb);
       bulk_commit();
     }
     const int nxt = si + ahead;
     if (nxt < a.SPG) {
-      // the buffer of strip nxt last held strip nxt - nbuf: wait until its
-      // store has left shared memory
+      // the buffer of strip nxt last held strip nxt - nbufs: its store must
+      // have left shared memory before the load (both issued by thread 0);
+      // its intensities and factors were last read before barrier B
       if (tid == 0) {
-        if (nbuf > ahead) bulk_wait_read<1>();
+        if (nbufs > ahead) bulk_wait_read<1>();
         else bulk_wait_read<0>();
       }
-      __syncthreads();
       issue(nxt);
     }
   }
@@ -326,11 +438,13 @@ __global__ void __launch_bounds__(kThreads, 2)
   float2* stage = work + C::GR * C::XB;
   float2* sbuf = work;
   float* ibuf = reinterpret_cast<float*>(work + (size_t)a.strip_bufs * a.M * N * kStripW);
+  float* fbuf = ibuf + (size_t)a.strip_bufs * N * kStripW;   // modulus factors of the current strip
+  float* nbuf = fbuf + N * kStripW;                          // norms when the modes take several rounds
   __shared__ __align__(8) uint64_t bars[kMaxStripBufs];
   __shared__ int s_task;
   __shared__ int s_skip;
   __shared__ double s_red[kThreads / 32];
-  for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
+  for (int i = threadIdx.x; i < tw_entries<N>(); i += kThreads) tw[i] = a.tw[i];
   if (threadIdx.x == 0) {
     for (int b = 0; b < kMaxStripBufs; ++b) mbar_init(&bars[b], 1);
     fence_mbar_init();
@@ -412,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       } else if (kind == 1) {
         const int jj = local / a.CG, sg = local % a.CG;
         const int j = c * a.B + jj;
-        double ef = column_task<N>(a, &tmap, sbuf, ibuf, tw, bars, pp, j, (sl * a.B + jj) * a.M, sg);
+        double ef = column_task<N>(a, &tmap, sbuf, ibuf, fbuf, nbuf, tw, bars, pp, j, (sl * a.B + jj) * a.M, sg);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ef += __shfl_xor_sync(0xffffffffu, ef, o);
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = ef;
@@ -443,6 +557,27 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
+template <int N>
+static int tw_host(float2* tab) {
+  if (tab)
+    tw_fill<N>(tab, [](int m) {
+      const double ang = -2.0 * 3.14159265358979323846 * (double)m / (double)N;
+      return make_float2((float)cos(ang), (float)sin(ang));
+    });
+  return tw_entries<N>();
+}
+
+int fourier_twiddles(int N, float2* tab) {
+  switch (N) {
+    case 16: return tw_host<16>(tab);
+    case 32: return tw_host<32>(tab);
+    case 64: return tw_host<64>(tab);
+    case 128: return tw_host<128>(tab);
+    case 256: return tw_host<256>(tab);
+    default: return 0;
+  }
+}
+
 int fourier_r2(int N) {
   switch (N) {
     case 16: return FftShape<16>::R2;
@@ -457,9 +592,14 @@ int fourier_r2(int N) {
 template <int N>
 static size_t smem_for(int M, int bufs) {
   using C = FCfg<N>;
-  const size_t rows = (size_t)C::GR * (C::XB + 2 * N);
-  const size_t cols = (size_t)bufs * M * N * kStripW + (size_t)bufs * N * kStripW / 2;
-  return 128 + kTwBytes + sizeof(float2) * (rows > cols ? rows : cols);
+  static_assert(tw_entries<N>() * sizeof(float2) <= kTwBytes, "twiddle tables exceed their shared area");
+  const size_t rows = sizeof(float2) * (size_t)C::GR * (C::XB + 2 * N);
+  const bool multi = M > CCfg<N>::SLOTS;
+  const size_t cols = sizeof(float2) * (size_t)bufs * M * N * kStripW      // strips
+                      + sizeof(float) * (size_t)bufs * N * kStripW         // their intensities
+                      + sizeof(float) * (size_t)N * kStripW                // modulus factors
+                      + (multi ? sizeof(float) * (size_t)M * N * kStripW : 0);  // norms (several rounds)
+  return 128 + kTwBytes + (rows > cols ? rows : cols);
 }
 
 size_t fourier_smem_bytes(int N, int M, int bufs) {

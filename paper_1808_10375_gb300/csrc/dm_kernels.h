@@ -38,14 +38,14 @@ struct FourierArgs {
   int N, M, J, H, W;
   float beta;
   float2* psi;            // [J][M][N][N]
-  const float* istrip;    // intensities in strip layout [J][NS][w][N]
+  const float* istrip;    // intensities in strip layout [J][NS][N][w]
   const float2* probe;    // [M][N][N]
   const float2* obj;      // [H][W]
   const int2* pos;        // [J] (row, col)
   float2* cview;          // [J][N][N] object source sum_k conj(P_k) psi_k
   float2* scratch;        // [nslot][B][M][N][N]
   double* ef_part;        // [J][CG] Fourier-error numerator partials
-  const float2* tw;       // [N] exp(-2 pi i m / N)
+  const float2* tw;       // twiddle tables (fourier_twiddles)
   int B, nchunks, lag, nslot;
   int RB;                 // row tasks per view (row blocks)
   int CG;                 // column tasks per view (strip groups)
@@ -125,6 +125,9 @@ cudaError_t launch_fourier(const void* tmap, const FourierArgs& a, int grid, siz
 size_t fourier_smem_bytes(int N, int M, int bufs);
 int fourier_occupancy(int N, size_t smem);
 int fourier_r2(int N);
+// Twiddle tables of the Fourier kernel for frame size N (entries written to
+// `tab` when non-null, double-precision angles); returns the entry count.
+int fourier_twiddles(int N, float2* tab);
 
 cudaError_t launch_obj_gather(const void* tmap, const ObjGatherArgs& a, int ntiles, cudaStream_t s);
 cudaError_t launch_obj_final(const ObjFinalArgs& a, int blocks, cudaStream_t s);

@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kThreads) k_init_psi(float2* psi, const float2
   }
 }
 
-// I[j][y][x] -> strip layout [j][s][c][y] with x = s*w + c; flags negative or
+// I[j][y][x] -> strip layout [j][s][y][c] with x = s*w + c; flags negative or
 // non-finite values; per-block FP64 partial sums of I.
 __global__ void __launch_bounds__(kThreads) k_intensity_layout(float* istrip, const float* inten, int N, int J,
                                                                int w, double* part, int* status) {
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kThreads) k_intensity_layout(float* istrip, co
     const float v = inten[i];
     if (!(v >= 0.f) || isinf(v)) bad = true;
     const int s = x / w, c = x % w;
-    istrip[j * nn + ((size_t)s * w + c) * N + y] = v;
+    istrip[j * nn + ((size_t)s * N + y) * w + c] = v;
     acc += (double)v;
   }
   if (bad) atomicOr(status, kStatusBadInput);

@@ -17,12 +17,12 @@ template <int N, bool INV>
 static double check(std::mt19937_64& rng) {
   constexpr int R1 = FftShape<N>::R1, R2 = FftShape<N>::R2, D = R1 / R2;
   std::normal_distribution<double> nd;
-  std::vector<float2> x(N), tw(N);
+  std::vector<float2> x(N), tw(tw_entries<N>());
   for (int i = 0; i < N; ++i) x[i] = make_float2((float)nd(rng), (float)nd(rng));
-  for (int m = 0; m < N; ++m) {
+  tw_fill<N>(tw.data(), [](int m) {
     const double a = -2.0 * M_PI * m / N;
-    tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
+    return make_float2((float)std::cos(a), (float)std::sin(a));
+  });
   // pass 1 per thread, exchange buffer [k1][t]
   std::vector<float2> xb(R1 * R2);
   for (int t = 0; t < R2; ++t) {
@@ -50,6 +50,48 @@ static double check(std::mt19937_64& rng) {
       im += x[n].x * std::sin(a) + x[n].y * std::cos(a);
     }
     num += (X[k].x - re) * (X[k].x - re) + (X[k].y - im) * (X[k].y - im);
+    den += re * re + im * im;
+  }
+  return std::sqrt(num / den);
+}
+
+// Inverse transform started from the pass-2 distribution (ifft_stepA, an
+// exchange, ifft_stepB) against the direct inverse DFT.
+template <int N>
+static double check_dif(std::mt19937_64& rng) {
+  constexpr int R1 = FftShape<N>::R1, R2 = FftShape<N>::R2, D = R1 / R2;
+  std::normal_distribution<double> nd;
+  std::vector<float2> X(N), tw(tw_entries<N>());
+  for (int i = 0; i < N; ++i) X[i] = make_float2((float)nd(rng), (float)nd(rng));
+  tw_fill<N>(tw.data(), [](int m) {
+    const double a = -2.0 * M_PI * m / N;
+    return make_float2((float)std::cos(a), (float)std::sin(a));
+  });
+  std::vector<float2> xb(R1 * R2);  // [k1][t]
+  for (int tp = 0; tp < R2; ++tp) {
+    float2 u[R1];
+    for (int d = 0; d < D; ++d)
+      for (int k2 = 0; k2 < R2; ++k2) u[p2_index<N>(d, k2)] = X[tp + R2 * d + R1 * k2];
+    ifft_stepA<N>(u, tp, tw_dif<N>(tw.data()));
+    for (int d = 0; d < D; ++d)
+      for (int t = 0; t < R2; ++t) xb[(tp + R2 * d) * R2 + t] = u[d * R2 + t];
+  }
+  std::vector<float2> x(N);
+  for (int t = 0; t < R2; ++t) {
+    float2 v[R1];
+    for (int k1 = 0; k1 < R1; ++k1) v[k1] = xb[k1 * R2 + t];
+    ifft_stepB<N>(v);
+    for (int i = 0; i < R1; ++i) x[t + R2 * i] = v[p1_index<N>(i)];
+  }
+  double num = 0, den = 0;
+  for (int n = 0; n < N; ++n) {
+    double re = 0, im = 0;
+    for (int k = 0; k < N; ++k) {
+      const double a = 2.0 * M_PI * (double)((long)n * k % N) / N;
+      re += X[k].x * std::cos(a) - X[k].y * std::sin(a);
+      im += X[k].x * std::sin(a) + X[k].y * std::cos(a);
+    }
+    num += (x[n].x - re) * (x[n].x - re) + (x[n].y - im) * (x[n].y - im);
     den += re * re + im * im;
   }
   return std::sqrt(num / den);
@@ -95,6 +137,9 @@ int main(int argc, char** argv) {
     rep("fft_fwd", 64, check<64, false>(rng));   rep("fft_inv", 64, check<64, true>(rng));
     rep("fft_fwd", 128, check<128, false>(rng)); rep("fft_inv", 128, check<128, true>(rng));
     rep("fft_fwd", 256, check<256, false>(rng)); rep("fft_inv", 256, check<256, true>(rng));
+    rep("ifft_dif", 16, check_dif<16>(rng));   rep("ifft_dif", 32, check_dif<32>(rng));
+    rep("ifft_dif", 64, check_dif<64>(rng));   rep("ifft_dif", 128, check_dif<128>(rng));
+    rep("ifft_dif", 256, check_dif<256>(rng));
   }
   std::printf("worst %.3e bound %.1e\n", worst, bound);
   return worst <= bound ? 0 : 1;
