@@ -55,12 +55,13 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, fl
   float2* xg = xb + g * C::XB;
   float2* srow_s = stage + g * N;              // staged psi row
   float2* prow_s = stage + (C::GR + g) * N;    // staged probe row
+  const uint64_t pol_first = l2_policy_evict_first(), pol_last = l2_policy_evict_last();
   auto issue = [&](int k) {
     const float2* src = a.psi + (((size_t)j * a.M + k) * N + y) * N;
     const float2* psrc = a.probe + ((size_t)k * N + y) * N;
     for (int q = t; q < N / 2; q += C::R2) {
-      cp_async16(srow_s + 2 * q, src + 2 * q);
-      cp_async16(prow_s + 2 * q, psrc + 2 * q);
+      cp_async16_hint(srow_s + 2 * q, src + 2 * q, pol_first);
+      cp_async16_hint(prow_s + 2 * q, psrc + 2 * q, pol_last);
     }
     cp_async_commit();
   };
@@ -92,7 +93,7 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, fl
 #pragma unroll
     for (int d = 0; d < C::D; ++d)
 #pragma unroll
-      for (int k2 = 0; k2 < C::R2; ++k2) __stcg(trow + t + C::R2 * d + C::R1 * k2, v[p2_index<N>(d, k2)]);
+      for (int k2 = 0; k2 < C::R2; ++k2) st_cg_hint(trow + t + C::R2 * d + C::R1 * k2, v[p2_index<N>(d, k2)], pol_last);
   }
 }
 
@@ -115,22 +116,27 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, fl
   float2* urow_s = stage + g * N;              // staged row of U
   float2* prow_s = stage + (C::GR + g) * N;    // staged probe row
   const float c2b = 2.f - a.beta;
+  const uint64_t pol_last = l2_policy_evict_last();
   auto stage_row = [&](float2* dst, const float2* src) {
-    for (int q = t; q < N / 2; q += C::R2) cp_async16(dst + 2 * q, src + 2 * q);
+    for (int q = t; q < N / 2; q += C::R2) cp_async16_hint(dst + 2 * q, src + 2 * q, pol_last);
     cp_async_commit();
   };
-  stage_row(urow_s, slot + (((size_t)jj * a.M) * N + y) * N);
+  auto urow_g = [&](int k) { return slot + (((size_t)jj * a.M + k) * N + y) * N; };
+  stage_row(urow_s, urow_g(0));
   stage_row(prow_s, a.probe + (size_t)y * N);
   float2 cacc[C::R1];
   for (int k = 0; k < a.M; ++k) {
     cp_async_wait<1>();   // U_k
     __syncwarp();
+    // this is the last read of the scratch row: drop its L2 lines unwritten
+    for (int q = t; q < N * (int)sizeof(float2) / 128; q += C::R2)
+      l2_discard128(reinterpret_cast<const char*>(urow_g(k)) + 128 * q);
     float2 v[C::R1];
 #pragma unroll
     for (int i = 0; i < C::R1; ++i) v[i] = urow_s[t + C::R2 * i];
     __syncwarp();
     const bool more = k + 1 < a.M;
-    if (more) stage_row(urow_s, slot + (((size_t)jj * a.M + k + 1) * N + y) * N);
+    if (more) stage_row(urow_s, urow_g(k + 1));
     fft_pass1<N, true>(v, t, twF);
     __syncwarp();
 #pragma unroll
@@ -339,16 +345,18 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
   // forward transform is done; otherwise in the separate buffer
   const int nstride = rounds == 1 ? 2 * N * SW : N * SW;   // floats per mode
   float ef = 0.f;  // this thread's few terms; the cross-thread sums are FP64
+  const uint64_t pol_first = l2_policy_evict_first(), pol_last = l2_policy_evict_last();
   auto issue = [&](int si) {  // strip si of the task into buffer si % nbufs (all threads)
     const int s = sg * a.SPG + si;
     const int b = si % nbufs;
     if (tid == 0) {
       mbar_arrive_expect_tx(&bars[b], strip_bytes);
-      tma_load_3d(sbuf + (size_t)b * strip_elems, tmap, s * SW, 0, zview, &bars[b]);
+      tma_load_3d_hint(sbuf + (size_t)b * strip_elems, tmap, s * SW, 0, zview, &bars[b], pol_last);
     }
     pp.issued[b]++;
     const float* ist = a.istrip + ((size_t)j * a.NS + s) * (N * SW);
-    for (int q = tid; q < (N * SW) / 4; q += kThreads) cp_async16(ibuf + b * (N * SW) + 4 * q, ist + 4 * q);
+    for (int q = tid; q < (N * SW) / 4; q += kThreads)
+      cp_async16_hint(ibuf + b * (N * SW) + 4 * q, ist + 4 * q, pol_first);
     cp_async_commit();
   };
   if (tid == 0) fence_proxy_async_global();
@@ -405,7 +413,7 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
     fence_proxy_async_smem();
     __syncthreads();   // C: U of every mode is in the strip
     if (tid == 0) {
-      tma_store_3d(tmap, s * SW, 0, zview, sb);
+      tma_store_3d_hint(tmap, s * SW, 0, zview, sb, pol_last);
       bulk_commit();
     }
     const int nxt = si + ahead;

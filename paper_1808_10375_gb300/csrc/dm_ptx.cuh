@@ -110,6 +110,24 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0,
       : "memory");
 }
 
+// 3-D tiled TMA load with an L2 policy.
+__device__ __forceinline__ void tma_load_3d_hint(void* dst, const void* tmap, int c0, int c1, int c2, uint64_t* bar,
+                                                 uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3, %4}], [%5], %6;"
+      ::"r"(smem_u32(dst)), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+
+// 3-D tiled TMA store with an L2 policy (bulk-group completion).
+__device__ __forceinline__ void tma_store_3d_hint(const void* tmap, int c0, int c1, int c2, const void* src,
+                                                  uint64_t pol) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2, %3}], [%4], %5;"
+               ::"l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src)), "l"(pol)
+               : "memory");
+}
+
 // 3-D tiled TMA store of one box from shared memory (bulk-group completion).
 __device__ __forceinline__ void tma_store_3d(const void* tmap, int c0, int c1, int c2, const void* src) {
   asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
@@ -179,6 +197,38 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
+// L2 eviction policies for the cache-hinted accesses below: streams read or
+// written once per iteration (exit waves, intensities) go first; the Fourier
+// scratch ring and the probe stay.
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// 16-byte asynchronous copy global -> shared (L1 bypassed) with an L2 policy.
+__device__ __forceinline__ void cp_async16_hint(void* dst, const void* src, uint64_t pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;"
+               ::"r"(smem_u32(dst)), "l"(src), "l"(pol) : "memory");
+}
+
+// 8-byte global store cached in L2 only, with an L2 policy.
+__device__ __forceinline__ void st_cg_hint(float2* dst, float2 v, uint64_t pol) {
+  asm volatile("st.global.cg.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;"
+               ::"l"(dst), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+}
+
+// Drop one 128-byte L2 line without writing it back (its contents become
+// undefined): for scratch whose last reader is done.
+__device__ __forceinline__ void l2_discard128(const void* p) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 template <int N>
