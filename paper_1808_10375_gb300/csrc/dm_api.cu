@@ -232,12 +232,9 @@ int plan_fourier(dm_ctx* c) {
   a.lw = 1;
   a.NS = N / a.w;
   const size_t strip_bytes = (size_t)M * N * a.w * sizeof(float2);
-  // Two strip buffers while they fit the budget; a third only where it does
-  // not enlarge the CTA beyond what the row tasks need (shared memory taken
-  // from L1 slows the row tasks, which read the object through L1).
-  a.strip_bufs = 2 * (strip_bytes + (size_t)N * a.w * sizeof(float)) <= kColumnSmemBudget ? 2 : 1;
-  if (a.strip_bufs == 2 && dmk::fourier_smem_bytes(N, M, 3) <= dmk::fourier_smem_bytes(N, M, 1))
-    a.strip_bufs = 3;
+  // Two strip buffers while they fit the budget, and a third (a strip and a
+  // half of prefetch) unless it costs a resident CTA (checked below).
+  a.strip_bufs = 2 * (strip_bytes + (size_t)N * a.w * sizeof(float)) <= kColumnSmemBudget ? 3 : 1;
   int spg = 1;
   while (spg * 2 <= a.NS && strip_bytes * spg * 2 <= kColumnTaskBytes) spg *= 2;
   a.SPG = spg;

@@ -36,15 +36,18 @@ struct FCfg {
   static constexpr int R1 = FftShape<N>::R1, R2 = FftShape<N>::R2, D = R1 / R2;
   static constexpr int GROUPS = kThreads / R2;          // transforms in flight per CTA
   static constexpr int GR = GROUPS < N ? GROUPS : N;     // rows per row task
-  static constexpr int XB = R1 * R2;                     // exchange buffer per transform (= N)
 };
 
 // ------------------------------------------------------------------ R task
-// The R2 lanes of a transform stage their row of psi and of P for the next
-// mode with 16-byte asynchronous copies while the current mode is computed;
-// the row buffers belong to the transform, so only warp-level sync is needed.
+// Each group of R2 lanes owns three row buffers: A stages psi of the next
+// mode, B stages P of the next mode and doubles as the exchange buffer of the
+// transform, O holds the object row (the same for every mode, staged once).
+// The copies are asynchronous (psi and P 16-byte, the object row 8-byte as
+// it starts at any column); the buffers belong to the group, so only
+// warp-level sync is needed.  psi, the stream from DRAM, is requested a whole
+// mode ahead; P (L2-resident) once the exchange has freed buffer B.
 template <int N>
-__device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, float2* stage, const float2* twF,
+__device__ __forceinline__ void row_forward(const FourierArgs& a, float2* stage, const float2* twF,
                                             int j, int jj, int rb, float2* slot) {
   using C = FCfg<N>;
   const int g = threadIdx.x / C::R2, t = threadIdx.x % C::R2;
@@ -52,20 +55,23 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, fl
   const int y = rb * C::GR + g;
   const int2 p = a.pos[j];
   const float2* orow = a.obj + (size_t)(p.x + y) * a.W + p.y;
-  float2* xg = xb + g * C::XB;
-  float2* srow_s = stage + g * N;              // staged psi row
-  float2* prow_s = stage + (C::GR + g) * N;    // staged probe row
+  float2* srow_s = stage + g * N;              // A: staged psi row
+  float2* prow_s = stage + (C::GR + g) * N;    // B: staged probe row, then the exchange
+  float2* orow_s = stage + (2 * C::GR + g) * N;  // O: object row
+  float2* xg = prow_s;
   const uint64_t pol_first = l2_policy_evict_first(), pol_last = l2_policy_evict_last();
-  auto issue = [&](int k) {
+  auto issue_psi = [&](int k) {
     const float2* src = a.psi + (((size_t)j * a.M + k) * N + y) * N;
-    const float2* psrc = a.probe + ((size_t)k * N + y) * N;
-    for (int q = t; q < N / 2; q += C::R2) {
-      cp_async16_hint(srow_s + 2 * q, src + 2 * q, pol_first);
-      cp_async16_hint(prow_s + 2 * q, psrc + 2 * q, pol_last);
-    }
-    cp_async_commit();
+    for (int q = t; q < N / 2; q += C::R2) cp_async16_hint(srow_s + 2 * q, src + 2 * q, pol_first);
   };
-  issue(0);
+  auto issue_p = [&](int k) {
+    const float2* src = a.probe + ((size_t)k * N + y) * N;
+    for (int q = t; q < N / 2; q += C::R2) cp_async16_hint(prow_s + 2 * q, src + 2 * q, pol_last);
+  };
+  for (int x = t; x < N; x += C::R2) cp_async8(orow_s + x, orow + x);
+  issue_psi(0);
+  issue_p(0);
+  cp_async_commit();
   for (int k = 0; k < a.M; ++k) {
     cp_async_wait<0>();
     __syncwarp();
@@ -73,14 +79,14 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, fl
 #pragma unroll
     for (int i = 0; i < C::R1; ++i) {
       const int x = t + C::R2 * i;
-      const float2 po = cmul(prow_s[x], __ldg(orow + x));
+      const float2 po = cmul(prow_s[x], orow_s[x]);
       const float2 s = srow_s[x];
       v[i] = make_float2(fmaf(2.f, po.x, -s.x), fmaf(2.f, po.y, -s.y));
     }
     __syncwarp();
-    if (k + 1 < a.M) issue(k + 1);
+    const bool more = k + 1 < a.M;
+    if (more) { issue_psi(k + 1); cp_async_commit(); }
     fft_pass1<N, false>(v, t, twF);
-    __syncwarp();
 #pragma unroll
     for (int k1 = 0; k1 < C::R1; ++k1) xg[k1 * C::R2 + (t ^ (k1 & (C::R2 - 1)))] = v[p1_index<N>(k1)];
     __syncwarp();
@@ -88,6 +94,8 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, fl
     for (int d = 0; d < C::D; ++d)
 #pragma unroll
       for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = xg[(t + C::R2 * d) * C::R2 + (tt ^ t)];
+    __syncwarp();
+    if (more) { issue_p(k + 1); cp_async_commit(); }
     fft_pass2<N, false>(v);
     float2* trow = slot + (((size_t)jj * a.M + k) * N + y) * N;
 #pragma unroll
@@ -98,13 +106,15 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* xb, fl
 }
 
 // ------------------------------------------------------------------ I task
-// The row of U for the next mode is staged (16-byte asynchronous copies) as
-// soon as the current one is in registers, and the probe row of the next mode
-// once the current epilogue has used its own; the object-source sum over the
-// modes stays in registers (each thread owns the same positions for every
-// mode).  Pending copy groups at the top of mode k: U_k, P_k.
+// Row buffers as in the R task: A stages U of the next mode and doubles as
+// the exchange buffer, B stages P of the next mode, O holds the object row.
+// U (L2-resident scratch) is requested once the exchange has freed buffer A;
+// P once the current epilogue has used its own.  The object-source sum over
+// the modes stays in registers (each thread owns the same positions for every
+// mode).  Pending copy groups at the top of mode k: U_k (with the object row
+// at k = 0), then P_k.
 template <int N>
-__device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, float2* stage, const float2* twF,
+__device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* stage, const float2* twF,
                                             int j, int jj, int rb, const float2* slot) {
   using C = FCfg<N>;
   const int g = threadIdx.x / C::R2, t = threadIdx.x % C::R2;
@@ -112,9 +122,10 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, fl
   const int y = rb * C::GR + g;
   const int2 p = a.pos[j];
   const float2* orow = a.obj + (size_t)(p.x + y) * a.W + p.y;
-  float2* xg = xb + g * C::XB;
-  float2* urow_s = stage + g * N;              // staged row of U
-  float2* prow_s = stage + (C::GR + g) * N;    // staged probe row
+  float2* urow_s = stage + g * N;              // A: staged row of U, then the exchange
+  float2* prow_s = stage + (C::GR + g) * N;    // B: staged probe row
+  float2* orow_s = stage + (2 * C::GR + g) * N;  // O: object row
+  float2* xg = urow_s;
   const float c2b = 2.f - a.beta;
   const uint64_t pol_last = l2_policy_evict_last();
   auto stage_row = [&](float2* dst, const float2* src) {
@@ -122,6 +133,7 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, fl
     cp_async_commit();
   };
   auto urow_g = [&](int k) { return slot + (((size_t)jj * a.M + k) * N + y) * N; };
+  for (int x = t; x < N; x += C::R2) cp_async8(orow_s + x, orow + x);
   stage_row(urow_s, urow_g(0));
   stage_row(prow_s, a.probe + (size_t)y * N);
   float2 cacc[C::R1];
@@ -136,9 +148,7 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, fl
     for (int i = 0; i < C::R1; ++i) v[i] = urow_s[t + C::R2 * i];
     __syncwarp();
     const bool more = k + 1 < a.M;
-    if (more) stage_row(urow_s, urow_g(k + 1));
     fft_pass1<N, true>(v, t, twF);
-    __syncwarp();
 #pragma unroll
     for (int k1 = 0; k1 < C::R1; ++k1) xg[k1 * C::R2 + (t ^ (k1 & (C::R2 - 1)))] = v[p1_index<N>(k1)];
     __syncwarp();
@@ -146,6 +156,8 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, fl
     for (int d = 0; d < C::D; ++d)
 #pragma unroll
       for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = xg[(t + C::R2 * d) * C::R2 + (tt ^ t)];
+    __syncwarp();
+    if (more) stage_row(urow_s, urow_g(k + 1));
     fft_pass2<N, true>(v);
     if (more) cp_async_wait<1>(); else cp_async_wait<0>();   // P_k
     __syncwarp();
@@ -156,7 +168,7 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* xb, fl
       for (int k2 = 0; k2 < C::R2; ++k2) {
         const int x = t + C::R2 * d + C::R1 * k2;
         const float2 pk = prow_s[x];
-        const float2 po = cmul(pk, __ldg(orow + x));
+        const float2 po = cmul(pk, orow_s[x]);
         const float2 g2 = v[p2_index<N>(d, k2)];
         const float2 pn = make_float2(fmaf(c2b, po.x, g2.x), fmaf(c2b, po.y, g2.y));
         __stcs(srow + x, pn);
@@ -179,7 +191,19 @@ struct Pipe {                     // per-thread bookkeeping of the strip barrier
   uint32_t done[kMaxStripBufs];    // TMA loads waited for
 };
 
+// Wait for the TMA load on barrier b: lane 0 of each warp polls (so that
+// spinning warps take few issue slots from co-resident tasks), then every
+// lane observes the completed phase itself.  All lanes of the warp call it.
 __device__ __forceinline__ void pipe_wait(Pipe& p, uint64_t* bars, int b, int* status) {
+  const uint32_t par = p.done[b] & 1u;
+  if ((threadIdx.x & 31) == 0) mbar_wait_bounded(&bars[b], par, status);
+  __syncwarp();
+  (void)mbar_try_wait_parity(&bars[b], par);
+  p.done[b]++;
+}
+
+// Single-thread form for the drain at the end of the kernel.
+__device__ __forceinline__ void pipe_drain(Pipe& p, uint64_t* bars, int b, int* status) {
   mbar_wait_bounded(&bars[b], p.done[b] & 1u, status);
   p.done[b]++;
 }
@@ -332,10 +356,6 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
   const float beta = a.beta;
   const int nbufs = a.strip_bufs;
   const float2* twD = tw_dif<N>(twF);
-  // strips loaded ahead of the one being transformed; with three buffers the
-  // buffer a new load goes to was stored from one strip earlier, so its
-  // store has had a whole strip's time to drain
-  const int ahead = nbufs < 2 ? nbufs : 2;
   const uint32_t strip_elems = (uint32_t)M * N * SW;
   const uint32_t strip_bytes = strip_elems * (uint32_t)sizeof(float2);
   const int slot = tid / C::TPM, c = tid & 1, t = (tid >> 1) & (C::R2 - 1);
@@ -359,9 +379,13 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
       cp_async16_hint(ibuf + b * (N * SW) + 4 * q, ist + 4 * q, pol_first);
     cp_async_commit();
   };
+  // Every buffer starts with a strip; later strips are issued in the middle
+  // of a strip (after barrier A), into the buffer whose TMA store was issued
+  // one strip earlier and has long left shared memory, so thread 0 does not
+  // wait for a store on the way between strips.
   if (tid == 0) fence_proxy_async_global();
-  issue(0);
-  if (ahead > 1 && a.SPG > 1) issue(1);
+  int issued = 0;
+  for (; issued < nbufs && issued < a.SPG; ++issued) issue(issued);
   for (int si = 0; si < a.SPG; ++si) {
     const int s = sg * a.SPG + si;
     const int b = si % nbufs;
@@ -389,8 +413,17 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
         }
       }
     }
-    if (ahead > 1 && si + 1 < a.SPG) cp_async_wait<1>(); else cp_async_wait<0>();
+    // intensities of strips after si may still be in flight (one group per strip)
+    const int later = issued - si - 1;
+    if (later >= 2) cp_async_wait<2>(); else if (later == 1) cp_async_wait<1>(); else cp_async_wait<0>();
     __syncthreads();   // A: every mode's norms (and this strip's intensities) are in place
+    if (issued < a.SPG && issued - si < nbufs) {
+      // strip `issued` goes to the buffer of strip issued - nbufs <= si - 1,
+      // whose store was committed before barrier C of that strip
+      if (tid == 0) bulk_wait_read<0>();   // at most the store of strip si - 1 is pending
+      issue(issued);
+      ++issued;
+    }
     ef = col_factor_any<N>(nrm, nstride, ib, fbuf, M, beta, ef);
     __syncthreads();   // B: the factors are in place; the norms are no longer read
     if (rounds == 1) {
@@ -416,16 +449,11 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
       tma_store_3d_hint(tmap, s * SW, 0, zview, sb, pol_last);
       bulk_commit();
     }
-    const int nxt = si + ahead;
-    if (nxt < a.SPG) {
-      // the buffer of strip nxt last held strip nxt - nbufs: its store must
-      // have left shared memory before the load (both issued by thread 0);
-      // its intensities and factors were last read before barrier B
-      if (tid == 0) {
-        if (nbufs > ahead) bulk_wait_read<1>();
-        else bulk_wait_read<0>();
-      }
-      issue(nxt);
+    if (nbufs == 1 && issued < a.SPG) {
+      // a single buffer: the next strip waits for this store to leave it
+      if (tid == 0) bulk_wait_read<0>();
+      issue(issued);
+      ++issued;
     }
   }
   return (double)ef;
@@ -442,8 +470,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   // row tasks: exchange buffers, then two row buffers per transform (staged
   // psi and P rows of R; the object-source accumulator of I); column tasks:
   // the strip buffers, then their intensities
-  float2* xb = work;
-  float2* stage = work + C::GR * C::XB;
+  float2* stage = work;
   float2* sbuf = work;
   float* ibuf = reinterpret_cast<float*>(work + (size_t)a.strip_bufs * a.M * N * kStripW);
   float* fbuf = ibuf + (size_t)a.strip_bufs * N * kStripW;   // modulus factors of the current strip
@@ -530,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       float2* slot = a.scratch + (size_t)sl * slot_elems;
       if (kind == 0) {
         const int jj = local / a.RB, rb = local % a.RB;
-        row_forward<N>(a, xb, stage, tw, c * a.B + jj, jj, rb, slot);
+        row_forward<N>(a, stage, tw, c * a.B + jj, jj, rb, slot);
       } else if (kind == 1) {
         const int jj = local / a.CG, sg = local % a.CG;
         const int j = c * a.B + jj;
@@ -546,10 +573,12 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
       } else {
         const int jj = local / a.RB, rb = local % a.RB;
-        row_inverse<N>(a, xb, stage, tw, c * a.B + jj, jj, rb, slot);
+        row_inverse<N>(a, stage, tw, c * a.B + jj, jj, rb, slot);
       }
     }
-    __threadfence();
+    // Publish the task: the barrier orders every thread's writes before
+    // thread 0's device-scope fence and counter update (a release by one
+    // thread after the barrier covers the whole CTA).
     __syncthreads();
     if (threadIdx.x == 0) {
       bulk_wait<0>();   // TMA stores of the task have landed
@@ -560,7 +589,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   // Copies that a timed-out wait left in flight must land before the CTA exits.
   if (threadIdx.x == 0) {
     for (int b = 0; b < kMaxStripBufs; ++b)
-      while (pp.done[b] < pp.issued[b]) pipe_wait(pp, bars, b, a.status);
+      while (pp.done[b] < pp.issued[b]) pipe_drain(pp, bars, b, a.status);
     bulk_wait<0>();
   }
 }
@@ -601,7 +630,7 @@ template <int N>
 static size_t smem_for(int M, int bufs) {
   using C = FCfg<N>;
   static_assert(tw_entries<N>() * sizeof(float2) <= kTwBytes, "twiddle tables exceed their shared area");
-  const size_t rows = sizeof(float2) * (size_t)C::GR * (C::XB + 2 * N);
+  const size_t rows = sizeof(float2) * (size_t)C::GR * 3 * N;   // three row buffers per transform
   const bool multi = M > CCfg<N>::SLOTS;
   const size_t cols = sizeof(float2) * (size_t)bufs * M * N * kStripW      // strips
                       + sizeof(float) * (size_t)bufs * N * kStripW         // their intensities
