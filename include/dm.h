@@ -194,6 +194,54 @@ int dm_probe_update_static(const float* psi, const float* object, const int32_t*
                            int32_t views, int32_t obj_h, int32_t obj_w, double denom_floor_rel,
                            void* stream);
 
+/* View-sharded overlap projection.  Sec. III spreads the views over GPUs:
+ * every rank runs the Fourier step on its own views, and the sums of Eq. 5
+ * and Eq. 4 over all views are formed by reducing per-rank partial sums
+ * (MPI reduce + broadcast in the paper).  These calls expose that split for
+ * a context that holds one shard of the views (same N, M, object size, beta
+ * and denom_floor_rel on every shard; the views of the shards together are
+ * the scan).  One iteration over S shard contexts, with "sum" any reduction
+ * over the shards (host, NCCL, ...):
+ *   for each shard: dm_run_step(DM_STEP_FOURIER)
+ *   for each shard: dm_object_partials(num_s, den_s);  sum -> num, den
+ *   for each shard: dm_object_apply(num, den)
+ *   for each shard: dm_probe_partials(pnum_s, pden_s); sum -> pnum, pden
+ *   for each shard: dm_probe_apply(pnum, pden)
+ *   for each shard: dm_fourier_error_partials(e_s);    sum -> e
+ *   for each shard: dm_finish_iteration(e)
+ * which equals dm_iterate(1) on the unsharded scan with n_inner = 1 and the
+ * probe updated (up to the order of the FP32 / FP64 sums).  Every shard ends
+ * with the same object and probe; each keeps its own exit waves.
+ *
+ * dm_object_partials: numerator and denominator of Eq. 5 over this
+ *   context's views, with the probe the Fourier step used:
+ *   num [H][W] complex (float pairs) = sum_jk conj(P_k(r-r_j)) psi_j^k(r-r_j),
+ *   den [H][W] float = sum_jk |P_k(r-r_j)|^2 (0 where no view of the shard
+ *   covers r).  Needs the Fourier step of this iteration to have run.
+ * dm_object_apply: the object update from the summed num, den (same layouts):
+ *   O = num / (den + delta), delta = denom_floor_rel * max(den); pixels with
+ *   den = 0 keep their value.  It becomes the current object.
+ * dm_probe_partials: numerator and denominator of Eq. 4 over this context's
+ *   views with the current object, in FP64: num [M][N][N][2] double,
+ *   den [N][N] double = sum_j |O(r_j+u)|^2.
+ * dm_probe_apply: P_k = num_k / (den + delta), delta = denom_floor_rel *
+ *   max(den); pixels with den = 0 keep their value.  It becomes the current
+ *   probe.
+ * dm_fourier_error_partials: sums[0] = sum_jq (sqrt S_j(q) - sqrt I_j(q))^2
+ *   and sums[1] = sum_jq I_j(q) over this context's views, from its last
+ *   Fourier step (host array of 2; synchronises).
+ * dm_finish_iteration: records the iteration's metrics (Eq. 6 from the
+ *   applied object and probe, E_F = sqrt(sums[0] / sums[1]) from the summed
+ *   `sums`, a host array of 2) and counts the iteration.
+ * num/den pointers follow mem_kind; the caller owns every buffer.  Errors:
+ * DM_EINVAL (NULL pointers, bad mem_kind), DM_ECUDA. */
+int dm_object_partials(dm_ctx* ctx, float* num, float* den, int32_t mem_kind);
+int dm_object_apply(dm_ctx* ctx, const float* num, const float* den, int32_t mem_kind);
+int dm_probe_partials(dm_ctx* ctx, double* num, double* den, int32_t mem_kind);
+int dm_probe_apply(dm_ctx* ctx, const double* num, const double* den, int32_t mem_kind);
+int dm_fourier_error_partials(dm_ctx* ctx, double* sums);
+int dm_finish_iteration(dm_ctx* ctx, const double* sums);
+
 /* Release everything the context holds (NULL is ignored). */
 void dm_free(dm_ctx* ctx);
 

@@ -74,6 +74,7 @@ struct dm_ctx {
   double* den_sum = nullptr;
   double* ring = nullptr;
   double* mode_pow = nullptr;
+  double* ef_tot = nullptr;   // [2] summed Fourier-error terms of a sharded iteration
   int cur_P = 0, cur_O = 0;
 
   dmk::FourierArgs fa{};
@@ -389,17 +390,21 @@ int run_fourier(dm_ctx* c) {
   return DM_OK;
 }
 
-// Eq. 5 into obj[nxt] from the current object sources; o_start = obj[cur].
-int run_object(dm_ctx* c) {
+// Eq. 5, part 1: numerator and denominator over the context's views from
+// the current object sources (num_O, den_O, and the maximum of den_O).
+int run_object_gather(dm_ctx* c) {
   DM_CUDA(c, cudaMemsetAsync(c->dmax_O, 0, sizeof(unsigned), c->stream));
   dmk::ObjGatherArgs g{};
   g.N = c->N; g.J = c->J; g.H = c->H; g.W = c->W; g.tiles_x = c->tiles_x;
   g.pos = c->pos; g.tile_ptr = c->tile_ptr; g.tile_views = c->tile_views; g.p2 = c->p2;
   g.num = c->num_O; g.den = c->den_O; g.den_max_bits = c->dmax_O; g.status = c->status;
-  {
-    Timed t(c, DM_KERNEL_OBJECT_GATHER);
-    DM_CUDA(c, dmk::launch_obj_gather(&c->tmap_c, g, c->tiles_x * c->tiles_y, c->stream));
-  }
+  Timed t(c, DM_KERNEL_OBJECT_GATHER);
+  DM_CUDA(c, dmk::launch_obj_gather(&c->tmap_c, g, c->tiles_x * c->tiles_y, c->stream));
+  return DM_OK;
+}
+
+// Eq. 5, part 2: obj[nxt] = num_O / (den_O + delta); o_start = obj[cur].
+int run_object_final(dm_ctx* c) {
   dmk::ObjFinalArgs f{};
   f.H = c->H; f.W = c->W; f.delta_rel = (float)c->p.denom_floor_rel;
   f.num = c->num_O; f.den = c->den_O; f.den_max_bits = c->dmax_O;
@@ -409,8 +414,25 @@ int run_object(dm_ctx* c) {
   return DM_OK;
 }
 
-// Eq. 4 into probe[nxt] from psi and object `o`; p_start = probe[cur].
-int run_probe(dm_ctx* c, const float2* o) {
+// Eq. 5 into obj[nxt] from the current object sources; o_start = obj[cur].
+int run_object(dm_ctx* c) {
+  int rc;
+  if ((rc = run_object_gather(c))) return rc;
+  return run_object_final(c);
+}
+
+dmk::ProbeFinalArgs probe_final_args(dm_ctx* c) {
+  dmk::ProbeFinalArgs f{};
+  f.N = c->N; f.M = c->M; f.groups = c->probe_groups; f.delta_rel = (float)c->p.denom_floor_rel;
+  f.part_num = c->part_num; f.part_den = c->part_den; f.p_start = c->probe[c->cur_P];
+  f.p_new = c->probe[c->cur_P ^ 1]; f.p2 = c->p2; f.num_sum = c->num_sum; f.den_sum = c->den_sum;
+  f.den_max_bits = c->dmax_P; f.part = c->probe_part;
+  return f;
+}
+
+// Eq. 4, part 1: per-group partial sums from psi and object `o`, then their
+// FP64 sums over the groups (num_sum, den_sum and the maximum of den_sum).
+int run_probe_sums(dm_ctx* c, const float2* o) {
   dmk::ProbePartialArgs a{};
   a.N = c->N; a.M = c->M; a.J = c->J; a.H = c->H; a.W = c->W; a.groups = c->probe_groups;
   a.psi = c->psi; a.obj = o; a.pos = c->pos; a.part_num = c->part_num; a.part_den = c->part_den;
@@ -420,14 +442,31 @@ int run_probe(dm_ctx* c, const float2* o) {
     DM_CUDA(c, dmk::launch_probe_partial(a, c->num_sms, c->stream));
   }
   DM_CUDA(c, cudaMemsetAsync(c->dmax_P, 0, sizeof(unsigned long long), c->stream));
-  dmk::ProbeFinalArgs f{};
-  f.N = c->N; f.M = c->M; f.groups = c->probe_groups; f.delta_rel = (float)c->p.denom_floor_rel;
-  f.part_num = c->part_num; f.part_den = c->part_den; f.p_start = c->probe[c->cur_P];
-  f.p_new = c->probe[c->cur_P ^ 1]; f.p2 = c->p2; f.num_sum = c->num_sum; f.den_sum = c->den_sum;
-  f.den_max_bits = c->dmax_P; f.part = c->probe_part;
+  Timed t(c, DM_KERNEL_PROBE_FINAL);
+  DM_CUDA(c, dmk::launch_probe_sum(probe_final_args(c), c->stream));
+  return DM_OK;
+}
+
+// Eq. 4, part 2: probe[nxt] = num_sum / (den_sum + delta); p_start = probe[cur].
+int run_probe_div(dm_ctx* c) {
   int blocks = 0;
   Timed t(c, DM_KERNEL_PROBE_FINAL);
-  DM_CUDA(c, dmk::launch_probe_final(f, c->stream, &blocks));
+  DM_CUDA(c, dmk::launch_probe_div(probe_final_args(c), c->stream, &blocks));
+  return DM_OK;
+}
+
+// Eq. 4 into probe[nxt] from psi and object `o`; p_start = probe[cur].
+int run_probe(dm_ctx* c, const float2* o) {
+  int rc;
+  if ((rc = run_probe_sums(c, o))) return rc;
+  return run_probe_div(c);
+}
+
+int run_metrics(dm_ctx* c, const double* ef, long long n_ef, const double* isum, bool upd) {
+  Timed t(c, DM_KERNEL_METRICS);
+  DM_CUDA(c, dmk::launch_metrics(ef, n_ef, isum, c->obj_part, c->obj_final_blocks, c->probe_part,
+                                 c->probe_final_blocks, c->M, upd ? 1 : 0, c->ring,
+                                 (int)(c->iters % dmk::kMetricsRing), c->status, c->stream));
   return DM_OK;
 }
 
@@ -542,6 +581,7 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   DM_TRY(alloc_n(c, &c->isum, 1));
   DM_TRY(alloc_n(c, &c->ring, (size_t)dmk::kMetricsRing * (2 + dmk::kMaxModes)));
   DM_TRY(alloc_n(c, &c->mode_pow, (size_t)M));
+  DM_TRY(alloc_n(c, &c->ef_tot, 2));
   if ((e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream)) != cudaSuccess) { cuda_fail(c, e, "memset"); return bail(DM_ECUDA); }
   if ((e = cudaMemsetAsync(c->ring, 0, sizeof(double) * dmk::kMetricsRing * (2 + dmk::kMaxModes), c->stream)) != cudaSuccess) {
     cuda_fail(c, e, "memset"); return bail(DM_ECUDA);
@@ -610,12 +650,7 @@ int dm_iterate(dm_ctx* c, int32_t n_iter) {
       if (!upd) break;  // later passes would repeat the same object update
       if ((rc = run_probe(c, c->obj[c->cur_O ^ 1]))) return rc;
     }
-    {
-      Timed t(c, DM_KERNEL_METRICS);
-      DM_CUDA(c, dmk::launch_metrics(c->ef_part, (long long)c->J * c->fa.CG, c->isum, c->obj_part,
-                                     c->obj_final_blocks, c->probe_part, c->probe_final_blocks, c->M, upd ? 1 : 0,
-                                     c->ring, (int)(c->iters % dmk::kMetricsRing), c->status, c->stream));
-    }
+    if ((rc = run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd))) return rc;
     c->cur_O ^= 1;
     if (upd) c->cur_P ^= 1;
     c->iters++;
@@ -645,6 +680,79 @@ int dm_run_step(dm_ctx* c, int32_t step) {
     default:
       return fail(c, DM_EINVAL, "unknown step");
   }
+}
+
+int dm_object_partials(dm_ctx* c, float* num, float* den, int32_t mem_kind) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!num || !den || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad output");
+  if ((rc = run_object_gather(c))) return rc;
+  const size_t hw = (size_t)c->H * c->W;
+  if ((rc = copy_out(c, num, c->num_O, hw * sizeof(float2), mem_kind))) return rc;
+  if ((rc = copy_out(c, den, c->den_O, hw * sizeof(float), mem_kind))) return rc;
+  return check_status(c);
+}
+
+int dm_object_apply(dm_ctx* c, const float* num, const float* den, int32_t mem_kind) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!num || !den || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad input");
+  const size_t hw = (size_t)c->H * c->W;
+  if ((rc = copy_in(c, c->num_O, num, hw * sizeof(float2), mem_kind))) return rc;
+  if ((rc = copy_in(c, c->den_O, den, hw * sizeof(float), mem_kind))) return rc;
+  DM_CUDA(c, cudaMemsetAsync(c->dmax_O, 0, sizeof(unsigned), c->stream));
+  DM_CUDA(c, dmk::launch_max_f32(c->den_O, hw, c->dmax_O, c->stream));
+  if ((rc = run_object_final(c))) return rc;
+  c->cur_O ^= 1;
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));   // the inputs may be host temporaries of the caller
+  return DM_OK;
+}
+
+int dm_probe_partials(dm_ctx* c, double* num, double* den, int32_t mem_kind) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!num || !den || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad output");
+  if ((rc = run_probe_sums(c, c->obj[c->cur_O]))) return rc;
+  const size_t nn = (size_t)c->N * c->N;
+  if ((rc = copy_out(c, num, c->num_sum, 2 * (size_t)c->M * nn * sizeof(double), mem_kind))) return rc;
+  if ((rc = copy_out(c, den, c->den_sum, nn * sizeof(double), mem_kind))) return rc;
+  return check_status(c);
+}
+
+int dm_probe_apply(dm_ctx* c, const double* num, const double* den, int32_t mem_kind) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!num || !den || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad input");
+  const size_t nn = (size_t)c->N * c->N;
+  if ((rc = copy_in(c, c->num_sum, num, 2 * (size_t)c->M * nn * sizeof(double), mem_kind))) return rc;
+  if ((rc = copy_in(c, c->den_sum, den, nn * sizeof(double), mem_kind))) return rc;
+  DM_CUDA(c, cudaMemsetAsync(c->dmax_P, 0, sizeof(unsigned long long), c->stream));
+  DM_CUDA(c, dmk::launch_max_f64(c->den_sum, nn, c->dmax_P, c->stream));
+  if ((rc = run_probe_div(c))) return rc;
+  c->cur_P ^= 1;
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DM_OK;
+}
+
+int dm_fourier_error_partials(dm_ctx* c, double* sums) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!sums) return fail(c, DM_EINVAL, "sums is NULL");
+  DM_CUDA(c, dmk::launch_reduce_sum(c->ef_part, (long long)c->J * c->fa.CG, 1, 0, c->ef_tot, c->stream));
+  DM_CUDA(c, cudaMemcpyAsync(c->ef_tot + 1, c->isum, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  if ((rc = copy_out(c, sums, c->ef_tot, 2 * sizeof(double), DM_HOST))) return rc;
+  return check_status(c);
+}
+
+int dm_finish_iteration(dm_ctx* c, const double* sums) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!sums) return fail(c, DM_EINVAL, "sums is NULL");
+  if ((rc = copy_in(c, c->ef_tot, sums, 2 * sizeof(double), DM_HOST))) return rc;
+  if ((rc = run_metrics(c, c->ef_tot, 1, c->ef_tot + 1, true))) return rc;
+  c->iters++;
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DM_OK;
 }
 
 int dm_get_object(dm_ctx* c, float* out, int32_t mem_kind) {

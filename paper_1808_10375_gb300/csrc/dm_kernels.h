@@ -139,6 +139,14 @@ size_t probe_partial_smem_bytes(int M);
 // Probe partial sums; a persistent grid of min(items, num_sms) CTAs.
 cudaError_t launch_probe_partial(const ProbePartialArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_probe_final(const ProbeFinalArgs& a, cudaStream_t s, int* blocks_out);
+// The two halves of launch_probe_final: FP64 sums over the view groups (and
+// max of the denominator), then the division and the Eq. 6 partials.
+cudaError_t launch_probe_sum(const ProbeFinalArgs& a, cudaStream_t s);
+cudaError_t launch_probe_div(const ProbeFinalArgs& a, cudaStream_t s, int* blocks_out);
+// Maximum of a non-negative array as the bit pattern in *bits (start at 0);
+// the f64 form records the float-rounded maximum.
+cudaError_t launch_max_f32(const float* x, size_t n, unsigned* bits, cudaStream_t s);
+cudaError_t launch_max_f64(const double* x, size_t n, unsigned long long* bits, cudaStream_t s);
 
 cudaError_t launch_init_psi(float2* psi, const float2* probe, const float2* obj, const int2* pos,
                             int N, int M, int J, int W, cudaStream_t s);

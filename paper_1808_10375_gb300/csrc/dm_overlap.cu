@@ -532,15 +532,47 @@ cudaError_t launch_probe_partial(const ProbePartialArgs& a, int num_sms, cudaStr
   return probe_partial_launch<16, 1>(a, num_sms, s);
 }
 
-// Runs 2a and 2b; *blocks_out receives the number of partial rows of 2b.
-cudaError_t launch_probe_final(const ProbeFinalArgs& a, cudaStream_t s, int* blocks_out) {
-  const int nn = a.N * a.N;
-  k_probe_sum<<<grid_for((size_t)(a.M + 1) * nn, 1024), kThreads, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int b = grid_for((size_t)nn, 256);
+cudaError_t launch_probe_sum(const ProbeFinalArgs& a, cudaStream_t s) {
+  k_probe_sum<<<grid_for((size_t)(a.M + 1) * (size_t)a.N * a.N, 1024), kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_div(const ProbeFinalArgs& a, cudaStream_t s, int* blocks_out) {
+  const int b = grid_for((size_t)a.N * a.N, 256);
   k_probe_div<<<b, kThreads, 0, s>>>(a);
   *blocks_out = b;
+  return cudaGetLastError();
+}
+
+// Runs 2a and 2b; *blocks_out receives the number of partial rows of 2b.
+cudaError_t launch_probe_final(const ProbeFinalArgs& a, cudaStream_t s, int* blocks_out) {
+  cudaError_t e = launch_probe_sum(a, s);
+  if (e != cudaSuccess) return e;
+  return launch_probe_div(a, s, blocks_out);
+}
+
+// Maximum of a non-negative array into *bits (as the bit pattern of the value,
+// which orders like the value for non-negative floats); *bits must start at 0.
+template <class T, class B>
+__global__ void __launch_bounds__(kThreads) k_max_nonneg(const T* x, size_t n, B* bits) {
+  __shared__ float shm[kThreads / 32];
+  float m = 0.f;
+  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kThreads)
+    m = fmaxf(m, (float)x[i]);
+  const float bm = block_max(m, shm);
+  if (threadIdx.x == 0 && bm > 0.f) {
+    if constexpr (sizeof(B) == 4) atomicMax(reinterpret_cast<unsigned*>(bits), __float_as_uint(bm));
+    else atomicMax(reinterpret_cast<unsigned long long*>(bits), (unsigned long long)__double_as_longlong((double)bm));
+  }
+}
+
+cudaError_t launch_max_f32(const float* x, size_t n, unsigned* bits, cudaStream_t s) {
+  k_max_nonneg<float, unsigned><<<grid_for(n, 4096), kThreads, 0, s>>>(x, n, bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_f64(const double* x, size_t n, unsigned long long* bits, cudaStream_t s) {
+  k_max_nonneg<double, unsigned long long><<<grid_for(n, 4096), kThreads, 0, s>>>(x, n, bits);
   return cudaGetLastError();
 }
 

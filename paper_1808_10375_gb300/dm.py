@@ -52,7 +52,9 @@ class DMError(RuntimeError):
 EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_object", "dm_get_probe",
            "dm_get_exit_waves", "dm_set_exit_waves", "dm_set_object", "dm_set_probe", "dm_get_error",
            "dm_iterations_done", "dm_get_mode_power", "dm_sync", "dm_set_timing", "dm_get_timing",
-           "dm_kernel_name", "dm_device_bytes", "dm_free", "dm_last_error", "dm_probe_update_static"]
+           "dm_kernel_name", "dm_device_bytes", "dm_free", "dm_last_error", "dm_probe_update_static",
+           "dm_object_partials", "dm_object_apply", "dm_probe_partials", "dm_probe_apply",
+           "dm_fourier_error_partials", "dm_finish_iteration"]
 
 _lib = None
 
@@ -90,6 +92,12 @@ def load(path: str = LIB_PATH):
         "dm_last_error": (ctypes.c_char_p, [vp]),
         "dm_probe_update_static": (ctypes.c_int, [vp, vp, vp, vp, vp, i32, i32, i32, i32, i32,
                                                   ctypes.c_double, vp]),
+        "dm_object_partials": (ctypes.c_int, [vp, vp, vp, i32]),
+        "dm_object_apply": (ctypes.c_int, [vp, vp, vp, i32]),
+        "dm_probe_partials": (ctypes.c_int, [vp, vp, vp, i32]),
+        "dm_probe_apply": (ctypes.c_int, [vp, vp, vp, i32]),
+        "dm_fourier_error_partials": (ctypes.c_int, [vp, dp]),
+        "dm_finish_iteration": (ctypes.c_int, [vp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -281,6 +289,79 @@ def dm_set_object(ctx: Context, obj):
 
 def dm_set_probe(ctx: Context, probe):
     _set(load().dm_set_probe, ctx, probe)
+
+
+def _buf(x, shape, np_dtype, device):
+    """(array, pointer, mem_kind) of a contiguous buffer of `np_dtype`: `x`
+    itself (NumPy array or torch tensor, host or CUDA) or a new one."""
+    if x is None:
+        if device:
+            import torch
+            tdt = {np.float32: torch.float32, np.float64: torch.float64, np.complex64: torch.complex64}[np_dtype]
+            x = torch.empty(shape, dtype=tdt, device="cuda")
+        else:
+            x = np.empty(shape, dtype=np_dtype)
+    if _is_torch(x):
+        import torch
+        tdt = {np.float32: torch.float32, np.float64: torch.float64, np.complex64: torch.complex64}[np_dtype]
+        if x.dtype != tdt or not x.is_contiguous() or tuple(x.shape) != tuple(shape):
+            raise ValueError(f"expected a contiguous {tdt} tensor of shape {shape}")
+        return x, x.data_ptr(), (DM_DEVICE if x.is_cuda else DM_HOST)
+    if x.dtype != np_dtype or not x.flags.c_contiguous or x.shape != tuple(shape):
+        raise ValueError(f"expected a contiguous {np_dtype.__name__} array of shape {shape}")
+    return x, x.ctypes.data, DM_HOST
+
+
+def dm_object_partials(ctx: Context, num=None, den=None, device=False):
+    """(num [H][W] complex64, den [H][W] float32) of Eq. 5 over the context's views."""
+    p = ctx.params
+    num, pn, mk = _buf(num, (p.obj_h, p.obj_w), np.complex64, device)
+    den, pd, mk2 = _buf(den, (p.obj_h, p.obj_w), np.float32, device)
+    if mk != mk2:
+        raise ValueError("num and den must both be host or both be device buffers")
+    _check(load().dm_object_partials(ctx.handle, pn, pd, mk), ctx)
+    return num, den
+
+
+def dm_object_apply(ctx: Context, num, den):
+    p = ctx.params
+    num, pn, mk = _buf(num, (p.obj_h, p.obj_w), np.complex64, False)
+    den, pd, mk2 = _buf(den, (p.obj_h, p.obj_w), np.float32, False)
+    if mk != mk2:
+        raise ValueError("num and den must both be host or both be device buffers")
+    _check(load().dm_object_apply(ctx.handle, pn, pd, mk), ctx)
+
+
+def dm_probe_partials(ctx: Context, num=None, den=None, device=False):
+    """(num [M][N][N][2] float64, den [N][N] float64) of Eq. 4 over the context's views."""
+    p = ctx.params
+    num, pn, mk = _buf(num, (p.modes, p.n, p.n, 2), np.float64, device)
+    den, pd, mk2 = _buf(den, (p.n, p.n), np.float64, device)
+    if mk != mk2:
+        raise ValueError("num and den must both be host or both be device buffers")
+    _check(load().dm_probe_partials(ctx.handle, pn, pd, mk), ctx)
+    return num, den
+
+
+def dm_probe_apply(ctx: Context, num, den):
+    p = ctx.params
+    num, pn, mk = _buf(num, (p.modes, p.n, p.n, 2), np.float64, False)
+    den, pd, mk2 = _buf(den, (p.n, p.n), np.float64, False)
+    if mk != mk2:
+        raise ValueError("num and den must both be host or both be device buffers")
+    _check(load().dm_probe_apply(ctx.handle, pn, pd, mk), ctx)
+
+
+def dm_fourier_error_partials(ctx: Context):
+    """[sum (sqrt S - sqrt I)^2, sum I] over the context's views (host)."""
+    out = (ctypes.c_double * 2)()
+    _check(load().dm_fourier_error_partials(ctx.handle, out), ctx)
+    return [out[0], out[1]]
+
+
+def dm_finish_iteration(ctx: Context, sums):
+    arr = (ctypes.c_double * 2)(float(sums[0]), float(sums[1]))
+    _check(load().dm_finish_iteration(ctx.handle, arr), ctx)
 
 
 def dm_get_error(ctx: Context, iteration: int = -1):
