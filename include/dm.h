@@ -164,6 +164,32 @@ int dm_set_timing(dm_ctx* ctx, int32_t enable);
 int dm_get_timing(dm_ctx* ctx, int32_t kernel, double* total_ms, int64_t* launches);
 const char* dm_kernel_name(int32_t kernel);
 
+/* Replay iterations as CUDA graphs (enable != 0) or launch every kernel
+ * (0, the default).  With graphs on, dm_iterate captures one iteration per
+ * pair of current object/probe buffers on first use (at most four graphs,
+ * kept until dm_free) and replays it; the results are the same.  Iterations
+ * with the probe frozen (probe_update_start) and iterations while timing is
+ * on are launched kernel by kernel.  The first dm_iterate after enabling
+ * performs the capture, so it must not itself run inside a stream capture. */
+int dm_set_graph(dm_ctx* ctx, int32_t enable);
+
+/* Choose the Fourier-step plan by measurement: every distinct combination
+ * of scratch-ring size (48, 64, 96, 128 MiB), column-task size (64, 128,
+ * 256 KiB of scratch) and strip buffers (2, 3) is timed on the first
+ * sample_views views of the context (one warm-up and three timed runs of the
+ * Fourier kernel each); the fastest is kept for the whole scan.  The exit
+ * waves of the sample views are restored afterwards; the object sources are
+ * recomputed by the next iteration, so results are unchanged.  Temporary
+ * buffers (up to the largest ring plus a copy of the sample's exit waves)
+ * come from the context's allocator.  *best_ms (if non-NULL) receives the
+ * winning time per run on the sample.  Synchronises.  Errors: DM_EINVAL,
+ * DM_ENOMEM, DM_ECUDA, DM_ETIMEOUT. */
+int dm_autotune(dm_ctx* ctx, int32_t sample_views, double* best_ms);
+
+/* The current Fourier-step plan: out[0] scratch-ring bytes, out[1] views per
+ * chunk, out[2] strips per column task, out[3] strip buffers, out[4] CTAs. */
+int dm_get_plan(const dm_ctx* ctx, int64_t* out);
+
 /* Bytes of device memory the context holds. */
 size_t dm_device_bytes(const dm_ctx* ctx);
 

@@ -26,6 +26,13 @@ constexpr int kFourierLag = 1;                   // stages between task kinds
 
 thread_local std::string g_init_error;
 
+// The tunable parts of the Fourier-step plan.
+struct FourierKnobs {
+  size_t budget;      // scratch ring bytes
+  size_t task_bytes;  // scratch bytes per column task (sets the strips per task)
+  int max_bufs;       // strip buffers of a column task, at most (1 to kMaxStripBufs)
+};
+
 struct TimedLaunch {
   int kind;
   cudaEvent_t start, stop;
@@ -75,9 +82,11 @@ struct dm_ctx {
   double* ring = nullptr;
   double* mode_pow = nullptr;
   double* ef_tot = nullptr;   // [2] summed Fourier-error terms of a sharded iteration
+  long long* iter_dev = nullptr;   // iterations recorded (picks the metrics ring slot on the device)
   int cur_P = 0, cur_O = 0;
 
   dmk::FourierArgs fa{};
+  FourierKnobs knobs{};
   int fgrid = 0;
   size_t fsmem = 0;
   size_t counters_bytes = 0;
@@ -87,6 +96,9 @@ struct dm_ctx {
   int probe_groups = 0;
   int probe_final_blocks = 0;
   int64_t iters = 0;
+  bool use_graph = false;
+  cudaStream_t cap_stream = nullptr;   // private stream the iteration graphs are captured on
+  cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // by (cur_O, cur_P)
 
   bool timing = false;
   std::vector<TimedLaunch> pending;
@@ -129,6 +141,17 @@ int dev_alloc(dm_ctx* c, void** out, size_t bytes) {
   return DM_OK;
 }
 
+// Release one allocation of the context (nullptr is ignored).
+void dev_free(dm_ctx* c, void* ptr) {
+  if (!ptr) return;
+  auto it = std::find_if(c->allocs.begin(), c->allocs.end(),
+                         [&](const std::pair<void*, size_t>& a) { return a.first == ptr; });
+  if (it == c->allocs.end()) return;
+  if (c->p.alloc) c->p.free(it->first, c->p.alloc_user); else cudaFreeAsync(it->first, c->stream);
+  c->bytes -= it->second;
+  c->allocs.erase(it);
+}
+
 template <typename T>
 int alloc_n(dm_ctx* c, T** out, size_t n) {
   return dev_alloc(c, reinterpret_cast<void**>(out), n * sizeof(T));
@@ -136,6 +159,10 @@ int alloc_n(dm_ctx* c, T** out, size_t n) {
 
 void release_all(dm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& row : c->gexec)
+    for (auto& g : row)
+      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  if (c->cap_stream) { cudaStreamDestroy(c->cap_stream); c->cap_stream = nullptr; }
   for (auto& a : c->allocs) {
     if (c->p.alloc && c->p.free) c->p.free(a.first, c->p.alloc_user);
     else if (!c->p.alloc) cudaFreeAsync(a.first, c->stream);
@@ -221,35 +248,45 @@ int copy_out(dm_ctx* c, void* dst, const void* src, size_t bytes, int mem_kind) 
 
 bool valid_n(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
 
-int plan_fourier(dm_ctx* c) {
-  const int N = c->N, M = c->M, J = c->J;
+FourierKnobs default_knobs(const dm_ctx* c) {
+  return {c->p.scratch_bytes > 0 ? (size_t)c->p.scratch_bytes : kScratchBudget, kColumnTaskBytes,
+          dmk::kMaxStripBufs};
+}
+
+// Host part of the plan for the first J views: the pipelined task order
+// (stage offsets), the scratch ring, the strip buffers and the launch shape.
+// Fills everything in `a` but the device pointers.
+int fourier_schedule(dm_ctx* c, int J, const FourierKnobs& k, dmk::FourierArgs& a, std::vector<int>& off,
+                     size_t& smem, int& grid) {
+  const int N = c->N, M = c->M;
   const int R2 = dmk::fourier_r2(N);
   const int groups = dmk::kThreads / R2;
   const int GR = std::min(groups, N);
-  dmk::FourierArgs& a = c->fa;
+  a = dmk::FourierArgs{};
   a.N = N; a.M = M; a.J = J; a.H = c->H; a.W = c->W;
   a.RB = N / GR;
   a.w = dmk::kStripW;
   a.lw = 1;
   a.NS = N / a.w;
   const size_t strip_bytes = (size_t)M * N * a.w * sizeof(float2);
-  // Two strip buffers while they fit the budget, and a third (a strip and a
-  // half of prefetch) unless it costs a resident CTA (checked below).
-  a.strip_bufs = 2 * (strip_bytes + (size_t)N * a.w * sizeof(float)) <= kColumnSmemBudget ? 3 : 1;
+  // Two or three strip buffers while two fit the shared-memory budget (a
+  // third gives a strip and a half of prefetch unless it costs a resident
+  // CTA, checked below), else one.
+  a.strip_bufs = 2 * (strip_bytes + (size_t)N * a.w * sizeof(float)) <= kColumnSmemBudget ? k.max_bufs : 1;
+  a.strip_bufs = std::max(1, std::min(a.strip_bufs, dmk::kMaxStripBufs));
   int spg = 1;
-  while (spg * 2 <= a.NS && strip_bytes * spg * 2 <= kColumnTaskBytes) spg *= 2;
+  while (spg * 2 <= a.NS && strip_bytes * spg * 2 <= k.task_bytes) spg *= 2;
   a.SPG = spg;
   a.CG = a.NS / spg;
   a.lag = kFourierLag;
   a.nslot = 2 * a.lag + 2;
   const size_t view_bytes = (size_t)M * N * N * sizeof(float2);
-  const size_t budget = c->p.scratch_bytes > 0 ? (size_t)c->p.scratch_bytes : kScratchBudget;
-  size_t B = budget / ((size_t)a.nslot * view_bytes);
+  size_t B = k.budget / ((size_t)a.nslot * view_bytes);
   B = std::max<size_t>(1, std::min<size_t>(B, (size_t)J));
   a.B = (int)B;
   a.nchunks = (J + a.B - 1) / a.B;
   a.nstages = a.nchunks + 2 * a.lag;
-  std::vector<int> off(a.nstages + 1, 0);
+  off.assign(a.nstages + 1, 0);
   auto nv = [&](int ch) { return std::min(a.B, J - ch * a.B); };
   long long total = 0;
   for (int s = 0; s < a.nstages; ++s) {
@@ -262,54 +299,67 @@ int plan_fourier(dm_ctx* c) {
   if (total >= (1ll << 31)) return fail(c, DM_EINVAL, "too many Fourier tasks");
   a.total_tasks = (int)total;
   a.beta = c->p.beta;
-  a.lw = 0;
-  while ((1 << a.lw) < a.w) ++a.lw;
-
-  int rc;
-  if ((rc = alloc_n(c, &c->scratch, (size_t)a.nslot * B * M * N * N))) return rc;
-  if ((rc = alloc_n(c, &c->stage_off, off.size()))) return rc;
-  c->counters_bytes = sizeof(int) * (1 + 3 * (size_t)a.nchunks);
-  if ((rc = dev_alloc(c, reinterpret_cast<void**>(&c->counters), c->counters_bytes))) return rc;
-  if ((rc = alloc_n(c, &c->ef_part, (size_t)J * a.CG))) return rc;
-  DM_CUDA(c, cudaMemcpyAsync(c->stage_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice,
-                             c->stream));
-  DM_CUDA(c, cudaStreamSynchronize(c->stream));  // `off` is a host temporary
-
-  // TMA view of the scratch ring for the column tasks: planes of N x N
-  // complex values (8-byte elements), one plane per (view, mode); a box is
-  // kStripW columns x N rows x M modes.
-  {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    DM_CUDA(c, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-    if (!fn || q != cudaDriverEntryPointSuccess) return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled unavailable");
-    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    const cuuint64_t e = sizeof(float2);
-    const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)a.nslot * B * M};
-    const cuuint64_t strides[2] = {(cuuint64_t)N * e, (cuuint64_t)N * N * e};
-    const cuuint32_t box[3] = {(cuuint32_t)a.w, (cuuint32_t)N, (cuuint32_t)M};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = encode(&c->tmap_s, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, c->scratch, dims, strides, box, estr,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS)
-      return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled (scratch) failed (" + std::to_string((int)r) + ")");
-  }
-  // a second strip buffer is only worth it while it costs no resident CTA
+  // an extra strip buffer is only worth it while it costs no resident CTA
   while (a.strip_bufs > 1 &&
          dmk::fourier_occupancy(N, dmk::fourier_smem_bytes(N, M, a.strip_bufs)) <
              dmk::fourier_occupancy(N, dmk::fourier_smem_bytes(N, M, a.strip_bufs - 1)))
     --a.strip_bufs;
-  c->fsmem = dmk::fourier_smem_bytes(N, M, a.strip_bufs);
-  const int occ = dmk::fourier_occupancy(N, c->fsmem);
+  smem = dmk::fourier_smem_bytes(N, M, a.strip_bufs);
+  const int occ = dmk::fourier_occupancy(N, smem);   // also sets the kernel's shared-memory limit
   if (occ < 1) return fail(c, DM_ECUDA, "Fourier kernel does not fit on an SM");
-  c->fgrid = std::max(1, std::min(a.total_tasks, occ * c->num_sms));
+  grid = std::max(1, std::min(a.total_tasks, occ * c->num_sms));
+  return DM_OK;
+}
 
+// TMA view of a scratch ring for the column tasks: planes of N x N complex
+// values (8-byte elements), one plane per (view, mode); a box is kStripW
+// columns x N rows x M modes.
+int encode_scratch_map(dm_ctx* c, const dmk::FourierArgs& a, float2* scratch, CUtensorMap* map) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  DM_CUDA(c, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+  if (!fn || q != cudaDriverEntryPointSuccess) return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const int N = a.N, M = a.M;
+  const cuuint64_t e = sizeof(float2);
+  const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)a.nslot * a.B * M};
+  const cuuint64_t strides[2] = {(cuuint64_t)N * e, (cuuint64_t)N * N * e};
+  const cuuint32_t box[3] = {(cuuint32_t)a.w, (cuuint32_t)N, (cuuint32_t)M};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, scratch, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled (scratch) failed (" + std::to_string((int)r) + ")");
+  return DM_OK;
+}
+
+size_t scratch_elems(const dmk::FourierArgs& a) { return (size_t)a.nslot * a.B * a.M * a.N * a.N; }
+
+// Plan the Fourier step of the whole scan with knobs `k` and allocate its
+// buffers (scratch ring, stage offsets, counters, Fourier-error partials).
+int plan_fourier(dm_ctx* c, const FourierKnobs& k) {
+  dmk::FourierArgs& a = c->fa;
+  std::vector<int> off;
+  int rc;
+  if ((rc = fourier_schedule(c, c->J, k, a, off, c->fsmem, c->fgrid))) return rc;
+  if ((rc = alloc_n(c, &c->scratch, scratch_elems(a)))) return rc;
+  if ((rc = alloc_n(c, &c->stage_off, off.size()))) return rc;
+  c->counters_bytes = sizeof(int) * (1 + 3 * (size_t)a.nchunks);
+  if ((rc = dev_alloc(c, reinterpret_cast<void**>(&c->counters), c->counters_bytes))) return rc;
+  if ((rc = alloc_n(c, &c->ef_part, (size_t)c->J * a.CG))) return rc;
+  DM_CUDA(c, cudaMemcpyAsync(c->stage_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             c->stream));
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));  // `off` is a host temporary
+  if ((rc = encode_scratch_map(c, a, c->scratch, &c->tmap_s))) return rc;
   a.psi = c->psi; a.istrip = c->istrip; a.pos = c->pos; a.cview = c->cview;
   a.scratch = c->scratch; a.ef_part = c->ef_part; a.tw = c->tw;
   a.stage_off = c->stage_off; a.counters = c->counters; a.status = c->status;
+  c->knobs = k;
   return DM_OK;
 }
+
+int plan_fourier(dm_ctx* c) { return plan_fourier(c, default_knobs(c)); }
 
 int plan_object(dm_ctx* c, const std::vector<int32_t>& hpos) {
   const int N = c->N, J = c->J;
@@ -362,6 +412,7 @@ int plan_object(dm_ctx* c, const std::vector<int32_t>& hpos) {
 }
 
 int plan_probe(dm_ctx* c) {
+  DM_CUDA(c, dmk::prepare_probe_partial(c->M));
   const int nn = c->N * c->N;
   const int tp = dmk::probe_tile_px(c->M);
   const int tiles = (nn + tp - 1) / tp;
@@ -465,8 +516,8 @@ int run_probe(dm_ctx* c, const float2* o) {
 int run_metrics(dm_ctx* c, const double* ef, long long n_ef, const double* isum, bool upd) {
   Timed t(c, DM_KERNEL_METRICS);
   DM_CUDA(c, dmk::launch_metrics(ef, n_ef, isum, c->obj_part, c->obj_final_blocks, c->probe_part,
-                                 c->probe_final_blocks, c->M, upd ? 1 : 0, c->ring,
-                                 (int)(c->iters % dmk::kMetricsRing), c->status, c->stream));
+                                 c->probe_final_blocks, c->M, upd ? 1 : 0, c->ring, c->iter_dev, c->status,
+                                 c->stream));
   return DM_OK;
 }
 
@@ -582,7 +633,9 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   DM_TRY(alloc_n(c, &c->ring, (size_t)dmk::kMetricsRing * (2 + dmk::kMaxModes)));
   DM_TRY(alloc_n(c, &c->mode_pow, (size_t)M));
   DM_TRY(alloc_n(c, &c->ef_tot, 2));
+  DM_TRY(alloc_n(c, &c->iter_dev, 1));
   if ((e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream)) != cudaSuccess) { cuda_fail(c, e, "memset"); return bail(DM_ECUDA); }
+  if ((e = cudaMemsetAsync(c->iter_dev, 0, sizeof(long long), c->stream)) != cudaSuccess) { cuda_fail(c, e, "memset"); return bail(DM_ECUDA); }
   if ((e = cudaMemsetAsync(c->ring, 0, sizeof(double) * dmk::kMetricsRing * (2 + dmk::kMaxModes), c->stream)) != cudaSuccess) {
     cuda_fail(c, e, "memset"); return bail(DM_ECUDA);
   }
@@ -634,27 +687,183 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   return DM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Every launch of one iteration (Eq. 3, then Eq. 5 and Eq. 4 n_inner times,
+// then Eq. 6), enqueued on the context's stream; no host state changes.
+int enqueue_iteration(dm_ctx* c, bool upd) {
+  int rc;
+  if ((rc = run_fourier(c))) return rc;
+  for (int pass = 0; pass < c->p.n_inner; ++pass) {
+    if (pass > 0) {
+      Timed t(c, DM_KERNEL_OTHER);
+      DM_CUDA(c, dmk::launch_obj_source(c->cview, c->psi, c->probe[c->cur_P ^ 1], c->N, c->M, c->J, c->stream));
+    }
+    if ((rc = run_object(c))) return rc;
+    if (!upd) break;  // later passes would repeat the same object update
+    if ((rc = run_probe(c, c->obj[c->cur_O ^ 1]))) return rc;
+  }
+  return run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd);
+}
+
+// The iteration for the current (object, probe) buffers as an instantiated
+// CUDA graph, captured on first use.
+int iteration_graph(dm_ctx* c, cudaGraphExec_t* out) {
+  cudaGraphExec_t& g = c->gexec[c->cur_O][c->cur_P];
+  if (!g) {
+    // Capture on a private stream (the context's stream may be the legacy
+    // default stream, which cannot be captured); the graph is then launched
+    // on the context's stream.
+    if (!c->cap_stream) DM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    DM_CUDA(c, cudaStreamSynchronize(c->stream));   // the graph must not overtake queued work
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    cudaError_t e0 = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e0 != cudaSuccess) { c->stream = user; return cuda_fail(c, e0, "cudaStreamBeginCapture"); }
+    const int rc = enqueue_iteration(c, true);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    c->stream = user;
+    if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    const cudaError_t e2 = cudaGraphInstantiate(&g, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) { g = nullptr; return cuda_fail(c, e2, "cudaGraphInstantiate"); }
+  }
+  *out = g;
+  return DM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int dm_iterate(dm_ctx* c, int32_t n_iter) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (n_iter < 0) return fail(c, DM_EINVAL, "n_iter must be >= 0");
   for (int it = 0; it < n_iter; ++it) {
     const bool upd = c->iters >= c->p.probe_update_start;
-    if ((rc = run_fourier(c))) return rc;
-    for (int pass = 0; pass < c->p.n_inner; ++pass) {
-      if (pass > 0) {
-        Timed t(c, DM_KERNEL_OTHER);
-        DM_CUDA(c, dmk::launch_obj_source(c->cview, c->psi, c->probe[c->cur_P ^ 1], c->N, c->M, c->J, c->stream));
-      }
-      if ((rc = run_object(c))) return rc;
-      if (!upd) break;  // later passes would repeat the same object update
-      if ((rc = run_probe(c, c->obj[c->cur_O ^ 1]))) return rc;
+    if (c->use_graph && upd && !c->timing) {
+      cudaGraphExec_t g = nullptr;
+      if ((rc = iteration_graph(c, &g))) return rc;
+      DM_CUDA(c, cudaGraphLaunch(g, c->stream));
+    } else if ((rc = enqueue_iteration(c, upd))) {
+      return rc;
     }
-    if ((rc = run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd))) return rc;
     c->cur_O ^= 1;
     if (upd) c->cur_P ^= 1;
     c->iters++;
   }
+  return DM_OK;
+}
+
+int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (sample_views < 1) return fail(c, DM_EINVAL, "sample_views must be >= 1");
+  const int Js = std::min<int>(sample_views, c->J);
+  const int N = c->N;
+  struct Plan {
+    FourierKnobs k;
+    dmk::FourierArgs a;
+    std::vector<int> off;
+    size_t smem;
+    int grid;
+  };
+  std::vector<Plan> plans;
+  size_t max_scr = 0, max_off = 0, max_cnt = 0;
+  for (size_t mb : {48, 64, 96, 128})
+    for (size_t kb : {64, 128, 256})
+      for (int b : {2, 3}) {
+        Plan pl;
+        pl.k = FourierKnobs{mb << 20, kb << 10, b};
+        if ((rc = fourier_schedule(c, Js, pl.k, pl.a, pl.off, pl.smem, pl.grid))) return rc;
+        bool dup = false;
+        for (const Plan& q : plans)
+          dup = dup || (q.a.B == pl.a.B && q.a.SPG == pl.a.SPG && q.a.strip_bufs == pl.a.strip_bufs);
+        if (dup) continue;
+        max_scr = std::max(max_scr, scratch_elems(pl.a));
+        max_off = std::max(max_off, pl.off.size());
+        max_cnt = std::max(max_cnt, 1 + 3 * (size_t)pl.a.nchunks);
+        plans.push_back(std::move(pl));
+      }
+  float2 *scr = nullptr, *psi_save = nullptr;
+  int *offd = nullptr, *cnt = nullptr;
+  double* ef = nullptr;
+  const size_t psi_elems = (size_t)Js * c->M * N * N;
+  auto release = [&]() {
+    cudaStreamSynchronize(c->stream);
+    for (void* q : {(void*)scr, (void*)psi_save, (void*)offd, (void*)cnt, (void*)ef}) dev_free(c, q);
+  };
+  if ((rc = alloc_n(c, &scr, max_scr)) || (rc = alloc_n(c, &psi_save, psi_elems)) ||
+      (rc = alloc_n(c, &offd, max_off)) || (rc = alloc_n(c, &cnt, max_cnt)) ||
+      (rc = alloc_n(c, &ef, (size_t)Js * (N / dmk::kStripW)))) {
+    release();
+    return rc;
+  }
+  // the tuning runs change the exit waves of the sample views: keep a copy
+  DM_CUDA(c, cudaMemcpyAsync(psi_save, c->psi, psi_elems * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+  cudaEvent_t e0 = take_event(c), e1 = take_event(c);
+  double best = 1e300;
+  FourierKnobs best_k = c->knobs;
+  constexpr int kReps = 3;
+  for (Plan& pl : plans) {
+    dmk::FourierArgs a = pl.a;
+    a.psi = c->psi; a.istrip = c->istrip; a.pos = c->pos; a.cview = c->cview; a.scratch = scr; a.ef_part = ef;
+    a.tw = c->tw; a.stage_off = offd; a.counters = cnt; a.status = c->status;
+    a.probe = c->probe[c->cur_P]; a.obj = c->obj[c->cur_O];
+    CUtensorMap map;
+    if ((rc = encode_scratch_map(c, a, scr, &map))) { release(); return rc; }
+    cudaError_t e = cudaMemcpyAsync(offd, pl.off.data(), pl.off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dmk::fourier_occupancy(N, pl.smem);   // sets the kernel's shared-memory limit for this plan
+    for (int r = 0; r <= kReps && e == cudaSuccess; ++r) {   // the first run warms up
+      if (r == 1) e = cudaEventRecord(e0, c->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 3 * (size_t)a.nchunks), c->stream);
+      if (e == cudaSuccess) e = dmk::launch_fourier(&map, a, pl.grid, pl.smem, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) { release(); return cuda_fail(c, e, "autotune run"); }
+    if (ms / kReps < best) { best = ms / kReps; best_k = pl.k; }
+  }
+  c->event_pool.push_back(e0);
+  c->event_pool.push_back(e1);
+  DM_CUDA(c, cudaMemcpyAsync(c->psi, psi_save, psi_elems * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+  release();
+  if ((rc = check_status(c))) return rc;
+  // re-plan the whole scan with the fastest knobs (captured graphs hold the
+  // old plan's arguments)
+  for (auto& row : c->gexec)
+    for (auto& g : row)
+      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  for (void* q : {(void*)c->scratch, (void*)c->stage_off, (void*)c->counters, (void*)c->ef_part}) dev_free(c, q);
+  c->scratch = nullptr; c->stage_off = nullptr; c->counters = nullptr; c->ef_part = nullptr;
+  if ((rc = plan_fourier(c, best_k))) return rc;
+  if (best_ms) *best_ms = best;
+  return DM_OK;
+}
+
+int dm_get_plan(const dm_ctx* c, int64_t* out) {
+  if (!c || !out) return DM_EINVAL;
+  out[0] = (int64_t)scratch_elems(c->fa) * (int64_t)sizeof(float2);
+  out[1] = c->fa.B;
+  out[2] = c->fa.SPG;
+  out[3] = c->fa.strip_bufs;
+  out[4] = c->fgrid;
+  return DM_OK;
+}
+
+int dm_set_graph(dm_ctx* c, int32_t enable) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  c->use_graph = enable != 0;
   return DM_OK;
 }
 

@@ -138,6 +138,7 @@ int probe_tile_px(int M);
 size_t probe_partial_smem_bytes(int M);
 // Probe partial sums; a persistent grid of min(items, num_sms) CTAs.
 cudaError_t launch_probe_partial(const ProbePartialArgs& a, int num_sms, cudaStream_t s);
+cudaError_t prepare_probe_partial(int M);
 cudaError_t launch_probe_final(const ProbeFinalArgs& a, cudaStream_t s, int* blocks_out);
 // The two halves of launch_probe_final: FP64 sums over the view groups (and
 // max of the denominator), then the division and the Eq. 6 partials.
@@ -157,7 +158,7 @@ cudaError_t launch_reduce_sum(const double* in, long long n, int stride, int off
                               cudaStream_t s);
 cudaError_t launch_metrics(const double* ef_part, long long n_ef, const double* isum,
                            const double* obj_part, int n_obj, const double* probe_part,
-                           int n_probe, int M, int probe_updated, double* ring, int slot,
+                           int n_probe, int M, int probe_updated, double* ring, long long* iter,
                            int* status, cudaStream_t s);
 cudaError_t launch_mode_power(const float2* probe, int N, int M, double* out, cudaStream_t s);
 

@@ -446,8 +446,15 @@ __global__ void __launch_bounds__(kThreads) k_reduce_sum(const double* in, long 
 __global__ void __launch_bounds__(kThreads) k_metrics(const double* ef_part, long long n_ef, const double* isum,
                                                       const double* obj_part, int n_obj,
                                                       const double* probe_part, int n_probe, int M,
-                                                      int probe_updated, double* ring, int slot, int* status) {
+                                                      int probe_updated, double* ring, long long* iter,
+                                                      int* status) {
   __shared__ double sh[kThreads / 32];
+  __shared__ int s_slot;
+  // the ring slot comes from the device-side iteration counter, so that a
+  // captured iteration can be replayed
+  if (threadIdx.x == 0) s_slot = (int)(*iter % kMetricsRing);
+  __syncthreads();
+  const int slot = s_slot;
   double ef = 0.0;
   for (long long i = threadIdx.x; i < n_ef; i += kThreads) ef += ef_part[i];
   ef = block_sum(ef, sh);
@@ -479,6 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_metrics(const double* ef_part, lon
     }
   }
   if (threadIdx.x == 0 && bad) atomicOr(status, kStatusNonFinite);
+  if (threadIdx.x == 0) *iter += 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -522,6 +530,19 @@ int probe_tile_px(int M) { return (M > 8 ? 1 : kProbePxPerThread) * kThreads; }
 
 size_t probe_partial_smem_bytes(int M) {
   return 128 + (size_t)kProbeStages * (M + 1) * probe_tile_px(M) * sizeof(float2);
+}
+
+// Sets the dynamic shared-memory limit of the probe-partial kernel for M
+// modes ahead of any launch (so that no attribute is set while a stream is
+// being captured).
+cudaError_t prepare_probe_partial(int M) {
+  const size_t smem = probe_partial_smem_bytes(M);
+  const void* f = M <= 1   ? (const void*)k_probe_partial<1, kProbePxPerThread>
+                  : M <= 2 ? (const void*)k_probe_partial<2, kProbePxPerThread>
+                  : M <= 4 ? (const void*)k_probe_partial<4, kProbePxPerThread>
+                  : M <= 8 ? (const void*)k_probe_partial<8, kProbePxPerThread>
+                           : (const void*)k_probe_partial<16, 1>;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 cudaError_t launch_probe_partial(const ProbePartialArgs& a, int num_sms, cudaStream_t s) {
@@ -602,9 +623,9 @@ cudaError_t launch_reduce_sum(const double* in, long long n, int stride, int off
 
 cudaError_t launch_metrics(const double* ef_part, long long n_ef, const double* isum, const double* obj_part,
                            int n_obj, const double* probe_part, int n_probe, int M, int probe_updated,
-                           double* ring, int slot, int* status, cudaStream_t s) {
+                           double* ring, long long* iter, int* status, cudaStream_t s) {
   k_metrics<<<1, kThreads, 0, s>>>(ef_part, n_ef, isum, obj_part, n_obj, probe_part, n_probe, M, probe_updated,
-                                   ring, slot, status);
+                                   ring, iter, status);
   return cudaGetLastError();
 }
 

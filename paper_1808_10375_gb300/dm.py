@@ -54,7 +54,8 @@ EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_
            "dm_iterations_done", "dm_get_mode_power", "dm_sync", "dm_set_timing", "dm_get_timing",
            "dm_kernel_name", "dm_device_bytes", "dm_free", "dm_last_error", "dm_probe_update_static",
            "dm_object_partials", "dm_object_apply", "dm_probe_partials", "dm_probe_apply",
-           "dm_fourier_error_partials", "dm_finish_iteration"]
+           "dm_fourier_error_partials", "dm_finish_iteration", "dm_set_graph", "dm_autotune",
+           "dm_get_plan"]
 
 _lib = None
 
@@ -98,6 +99,9 @@ def load(path: str = LIB_PATH):
         "dm_probe_apply": (ctypes.c_int, [vp, vp, vp, i32]),
         "dm_fourier_error_partials": (ctypes.c_int, [vp, dp]),
         "dm_finish_iteration": (ctypes.c_int, [vp, dp]),
+        "dm_set_graph": (ctypes.c_int, [vp, i32]),
+        "dm_autotune": (ctypes.c_int, [vp, i32, dp]),
+        "dm_get_plan": (ctypes.c_int, [vp, P(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -230,6 +234,25 @@ def dm_init(params: dm_params, positions, intensities, probe0, object0, use_torc
 
 def dm_iterate(ctx: Context, n_iter: int = 1):
     return _check(load().dm_iterate(ctx.handle, int(n_iter)), ctx)
+
+
+def dm_set_graph(ctx: Context, enable: bool = True):
+    return _check(load().dm_set_graph(ctx.handle, 1 if enable else 0), ctx)
+
+
+def dm_autotune(ctx: Context, sample_views: int = 500) -> float:
+    """Time the candidate Fourier-step plans on the first views; keeps the
+    fastest.  Returns its time per run (ms) on the sample."""
+    best = ctypes.c_double()
+    _check(load().dm_autotune(ctx.handle, int(sample_views), ctypes.byref(best)), ctx)
+    return best.value
+
+
+def dm_get_plan(ctx: Context) -> dict:
+    out = (ctypes.c_int64 * 5)()
+    _check(load().dm_get_plan(ctx.handle, out), ctx)
+    return dict(scratch_bytes=out[0], views_per_chunk=out[1], strips_per_column_task=out[2],
+                strip_buffers=out[3], ctas=out[4])
 
 
 def dm_run_step(ctx: Context, step: int):
