@@ -190,6 +190,27 @@ int dm_autotune(dm_ctx* ctx, int32_t sample_views, double* best_ms);
  * chunk, out[2] strips per column task, out[3] strip buffers, out[4] CTAs. */
 int dm_get_plan(const dm_ctx* ctx, int64_t* out);
 
+/* Several scans advanced together (the batched form).  The contexts (same
+ * device; any frame sizes, mode and view counts) keep their own data and
+ * plans; an iteration of the batch runs, for each frame size, one persistent
+ * Fourier-step launch over all scans of that size (up to 16 per launch; more
+ * scans take further launches), then each scan's object and probe updates
+ * and metrics.  Each scan's results equal those of dm_iterate on it alone.
+ * The work runs on a stream the batch owns, ordered after the work queued on
+ * every context's stream and before work queued on them afterwards.
+ * dm_batch_set_graph(b, 1) captures a batch iteration as one CUDA graph per
+ * combination of the scans' current buffers and replays it (iterations with
+ * a frozen probe or with timing on are launched kernel by kernel).
+ * The contexts must outlive the batch, and no other call may use them while
+ * dm_batch_iterate runs.  Errors: DM_EINVAL, DM_ECUDA, DM_ENOMEM; the message
+ * is in dm_batch_last_error (NULL: the last failed dm_batch_create). */
+typedef struct dm_batch dm_batch;
+int dm_batch_create(dm_batch** out, dm_ctx* const* ctxs, int32_t count);
+int dm_batch_iterate(dm_batch* batch, int32_t n_iter);
+int dm_batch_set_graph(dm_batch* batch, int32_t enable);
+void dm_batch_free(dm_batch* batch);
+const char* dm_batch_last_error(const dm_batch* batch);
+
 /* Bytes of device memory the context holds. */
 size_t dm_device_bytes(const dm_ctx* ctx);
 

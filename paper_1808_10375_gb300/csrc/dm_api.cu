@@ -860,6 +860,211 @@ int dm_get_plan(const dm_ctx* c, int64_t* out) {
   return DM_OK;
 }
 
+}  // extern "C"
+
+// A batch of contexts advanced together: per frame size, one persistent
+// Fourier launch over all its scans (at most kMaxBatchScans per launch),
+// then each scan's overlap projection and metrics, all on the batch's
+// stream.
+struct dm_batch {
+  std::vector<dm_ctx*> ctx;
+  struct Group {
+    int N = 0;
+    std::vector<int> scans;
+    size_t smem = 0;
+    int grid = 0;
+  };
+  std::vector<Group> groups;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int* dispensers = nullptr;   // one per group
+  cudaEvent_t ev = nullptr;
+  bool use_graph = false;
+  std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> graphs;   // by the scans' buffer parities
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+int batch_fail(dm_batch* b, int code, const std::string& msg) {
+  if (b) b->err = msg; else g_batch_error = msg;
+  return code;
+}
+
+#define DM_BCUDA(b, call)                                                               \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return batch_fail(b, DM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Every launch of one batch iteration on the batch's stream.
+int enqueue_batch_iteration(dm_batch* b) {
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    auto& g = b->groups[gi];
+    dmk::FourierBatch fb{};
+    fb.nscan = (int)g.scans.size();
+    fb.dispenser = b->dispensers + gi;
+    int base = 0;
+    for (int s = 0; s < fb.nscan; ++s) {
+      dm_ctx* c = b->ctx[g.scans[s]];
+      c->fa.probe = c->probe[c->cur_P];
+      c->fa.obj = c->obj[c->cur_O];
+      fb.a[s] = c->fa;
+      fb.map[s] = c->tmap_s;
+      fb.base[s] = base;
+      base += c->fa.total_tasks;
+      DM_BCUDA(b, cudaMemsetAsync(c->counters, 0, c->counters_bytes, b->stream));
+    }
+    fb.base[fb.nscan] = base;
+    DM_BCUDA(b, cudaMemsetAsync(fb.dispenser, 0, sizeof(int), b->stream));
+    DM_BCUDA(b, dmk::launch_fourier_batch(fb, g.N, g.grid, g.smem, b->stream));
+  }
+  for (dm_ctx* c : b->ctx) {
+    const bool upd = c->iters >= c->p.probe_update_start;
+    cudaStream_t own = c->stream;
+    c->stream = b->stream;
+    int rc = DM_OK;
+    for (int pass = 0; pass < c->p.n_inner && rc == DM_OK; ++pass) {
+      if (pass > 0) {
+        const cudaError_t e = dmk::launch_obj_source(c->cview, c->psi, c->probe[c->cur_P ^ 1], c->N, c->M, c->J,
+                                                     c->stream);
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "object source");
+      }
+      if (rc == DM_OK) rc = run_object(c);
+      if (!upd) break;
+      if (rc == DM_OK) rc = run_probe(c, c->obj[c->cur_O ^ 1]);
+    }
+    if (rc == DM_OK) rc = run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd);
+    c->stream = own;
+    if (rc) return batch_fail(b, rc, c->err);
+  }
+  return DM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dm_batch_create(dm_batch** out, dm_ctx* const* ctxs, int32_t count) {
+  g_batch_error.clear();
+  if (!out) return batch_fail(nullptr, DM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!ctxs || count < 1) return batch_fail(nullptr, DM_EINVAL, "no contexts");
+  auto* b = new dm_batch();
+  b->device = ctxs[0]->device;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) { delete b; return batch_fail(nullptr, DM_EINVAL, "a context is NULL"); }
+    if (ctxs[i]->device != b->device) { delete b; return batch_fail(nullptr, DM_EINVAL, "contexts on different devices"); }
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) { delete b; return batch_fail(nullptr, DM_EINVAL, "a context appears twice"); }
+    b->ctx.push_back(ctxs[i]);
+  }
+  cudaSetDevice(b->device);
+  for (int i = 0; i < count; ++i) {
+    const int N = b->ctx[i]->N;
+    dm_batch::Group* g = nullptr;
+    for (auto& q : b->groups)
+      if (q.N == N && (int)q.scans.size() < dmk::kMaxBatchScans) g = &q;
+    if (!g) { b->groups.emplace_back(); g = &b->groups.back(); g->N = N; }
+    g->scans.push_back(i);
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  for (auto& g : b->groups) {
+    long long tasks = 0;
+    for (int s : g.scans) {
+      g.smem = std::max(g.smem, b->ctx[s]->fsmem);
+      tasks += b->ctx[s]->fa.total_tasks;
+    }
+    const int occ = dmk::fourier_batch_occupancy(g.N, g.smem);
+    if (occ < 1) { delete b; return batch_fail(nullptr, DM_ECUDA, "batched Fourier kernel does not fit on an SM"); }
+    g.grid = (int)std::max<long long>(1, std::min<long long>(tasks, (long long)occ * sms));
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&b->dispensers), sizeof(int) * b->groups.size(), b->stream);
+  if (e != cudaSuccess) {
+    if (b->ev) cudaEventDestroy(b->ev);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return batch_fail(nullptr, DM_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return DM_OK;
+}
+
+int dm_batch_iterate(dm_batch* b, int32_t n_iter) {
+  if (!b) return DM_EINVAL;
+  if (n_iter < 0) return batch_fail(b, DM_EINVAL, "n_iter must be >= 0");
+  DM_BCUDA(b, cudaSetDevice(b->device));
+  // the batch's stream follows the work queued on every context's stream
+  for (dm_ctx* c : b->ctx) {
+    DM_BCUDA(b, cudaEventRecord(b->ev, c->stream));
+    DM_BCUDA(b, cudaStreamWaitEvent(b->stream, b->ev, 0));
+  }
+  for (int it = 0; it < n_iter; ++it) {
+    bool graph_ok = b->use_graph;
+    std::vector<int> key;
+    for (dm_ctx* c : b->ctx) {
+      graph_ok = graph_ok && !c->timing && c->iters >= c->p.probe_update_start;
+      key.push_back(c->cur_O * 2 + c->cur_P);
+    }
+    if (graph_ok) {
+      cudaGraphExec_t g = nullptr;
+      for (auto& kv : b->graphs)
+        if (kv.first == key) g = kv.second;
+      if (!g) {
+        DM_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue_batch_iteration(b);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+        if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+        DM_BCUDA(b, e);
+        const cudaError_t e2 = cudaGraphInstantiate(&g, graph, 0);
+        cudaGraphDestroy(graph);
+        DM_BCUDA(b, e2);
+        b->graphs.emplace_back(key, g);
+      }
+      DM_BCUDA(b, cudaGraphLaunch(g, b->stream));
+    } else {
+      const int rc = enqueue_batch_iteration(b);
+      if (rc) return rc;
+    }
+    for (dm_ctx* c : b->ctx) {
+      const bool upd = c->iters >= c->p.probe_update_start;
+      c->cur_O ^= 1;
+      if (upd) c->cur_P ^= 1;
+      c->iters++;
+    }
+  }
+  // and every context's stream follows the batch
+  DM_BCUDA(b, cudaEventRecord(b->ev, b->stream));
+  for (dm_ctx* c : b->ctx) DM_BCUDA(b, cudaStreamWaitEvent(c->stream, b->ev, 0));
+  return DM_OK;
+}
+
+int dm_batch_set_graph(dm_batch* b, int32_t enable) {
+  if (!b) return DM_EINVAL;
+  b->use_graph = enable != 0;
+  return DM_OK;
+}
+
+void dm_batch_free(dm_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  if (b->dispensers) cudaFreeAsync(b->dispensers, b->stream);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+const char* dm_batch_last_error(const dm_batch* b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
 int dm_set_graph(dm_ctx* c, int32_t enable) {
   int rc = check_ctx(c);
   if (rc) return rc;

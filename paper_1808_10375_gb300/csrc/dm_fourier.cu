@@ -459,50 +459,58 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
   return (double)ef;
 }
 
-template <int N>
-__global__ void __launch_bounds__(kThreads, 2)
-    k_fourier(const __grid_constant__ CUtensorMap tmap, const FourierArgs a) {
-  using C = FCfg<N>;
+// The persistent task loop over one or more scans of frame size N.  Scan s
+// owns tasks [base[s], base[s+1]) of the launch's counter `disp`; within a
+// scan the order and dependencies are those of its own plan (stage offsets,
+// per-chunk counters, scratch ring).  A CTA's tasks increase, so it moves
+// through the scans in order.
+template <int N, bool BATCH>
+__device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUtensorMap* maps, const int* base,
+                                              int nscan, int* disp) {
   extern __shared__ unsigned char smem_raw[];
   // 128-byte aligned base (TMA boxes land at 128-byte aligned addresses)
   float2* tw = reinterpret_cast<float2*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
   float2* work = tw + kTwBytes / sizeof(float2);
-  // row tasks: exchange buffers, then two row buffers per transform (staged
-  // psi and P rows of R; the object-source accumulator of I); column tasks:
-  // the strip buffers, then their intensities
+  // row tasks: three row buffers per transform; column tasks: the strip
+  // buffers, then their intensities, the modulus factors and (with several
+  // rounds of modes) the norms, laid out for the scan of the task
   float2* stage = work;
   float2* sbuf = work;
-  float* ibuf = reinterpret_cast<float*>(work + (size_t)a.strip_bufs * a.M * N * kStripW);
-  float* fbuf = ibuf + (size_t)a.strip_bufs * N * kStripW;   // modulus factors of the current strip
-  float* nbuf = fbuf + N * kStripW;                          // norms when the modes take several rounds
   __shared__ __align__(8) uint64_t bars[kMaxStripBufs];
   __shared__ int s_task;
   __shared__ int s_skip;
   __shared__ double s_red[kThreads / 32];
-  for (int i = threadIdx.x; i < tw_entries<N>(); i += kThreads) tw[i] = a.tw[i];
+  for (int i = threadIdx.x; i < tw_entries<N>(); i += kThreads) tw[i] = as[0].tw[i];
   if (threadIdx.x == 0) {
     for (int b = 0; b < kMaxStripBufs; ++b) mbar_init(&bars[b], 1);
     fence_mbar_init();
   }
   Pipe pp = {};
-
-  int* disp = a.counters;
-  int* doneR = a.counters + 1;
-  int* doneC = doneR + a.nchunks;
-  int* doneI = doneC + a.nchunks;
+  const int total = BATCH ? base[nscan] : as[0].total_tasks;
   int next = 0;
   if (threadIdx.x == 0) next = atomicAdd(disp, 1);
-  int st_prev = 0;
-  const size_t slot_elems = (size_t)a.B * a.M * N * N;
+  int st_prev = 0, scan_prev = 0;
 
   for (;;) {
     if (threadIdx.x == 0) {
       s_task = next;
-      if (next < a.total_tasks) next = atomicAdd(disp, 1);
+      if (next < total) next = atomicAdd(disp, 1);
     }
     __syncthreads();
-    const int task = s_task;
-    if (task >= a.total_tasks) break;
+    const int gtask = s_task;
+    if (gtask >= total) break;
+    int sc = 0;
+    if constexpr (BATCH) {
+      sc = scan_prev;
+      while (base[sc + 1] <= gtask) ++sc;
+      if (sc != scan_prev) { scan_prev = sc; st_prev = 0; }
+    }
+    const FourierArgs& a = as[sc];
+    const int task = BATCH ? gtask - base[sc] : gtask;
+    int* doneR = a.counters + 1;
+    int* doneC = doneR + a.nchunks;
+    int* doneI = doneC + a.nchunks;
+    const size_t slot_elems = (size_t)a.B * a.M * N * N;
 
     // Decode (stage, kind, chunk, local index).  A CTA's tasks increase, so
     // the stage is the previous one or a later one: look at the next stage
@@ -561,7 +569,11 @@ __global__ void __launch_bounds__(kThreads, 2)
       } else if (kind == 1) {
         const int jj = local / a.CG, sg = local % a.CG;
         const int j = c * a.B + jj;
-        double ef = column_task<N>(a, &tmap, sbuf, ibuf, fbuf, nbuf, tw, bars, pp, j, (sl * a.B + jj) * a.M, sg);
+        float* ibuf = reinterpret_cast<float*>(work + (size_t)a.strip_bufs * a.M * N * kStripW);
+        float* fbuf = ibuf + (size_t)a.strip_bufs * N * kStripW;   // modulus factors of the current strip
+        float* nbuf = fbuf + N * kStripW;                          // norms when the modes take several rounds
+        double ef = column_task<N>(a, maps + sc, sbuf, ibuf, fbuf, nbuf, tw, bars, pp, j, (sl * a.B + jj) * a.M,
+                                   sg);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ef += __shfl_xor_sync(0xffffffffu, ef, o);
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = ef;
@@ -589,9 +601,22 @@ __global__ void __launch_bounds__(kThreads, 2)
   // Copies that a timed-out wait left in flight must land before the CTA exits.
   if (threadIdx.x == 0) {
     for (int b = 0; b < kMaxStripBufs; ++b)
-      while (pp.done[b] < pp.issued[b]) pipe_drain(pp, bars, b, a.status);
+      while (pp.done[b] < pp.issued[b]) pipe_drain(pp, bars, b, as[0].status);
     bulk_wait<0>();
   }
+}
+
+// One scan: its task counter is counters[0].
+template <int N>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_fourier(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ FourierArgs a) {
+  fourier_tasks<N, false>(&a, &tmap, nullptr, 1, a.counters);
+}
+
+// Several scans of the same frame size in one persistent launch.
+template <int N>
+__global__ void __launch_bounds__(kThreads, 2) k_fourier_batch(const __grid_constant__ FourierBatch b) {
+  fourier_tasks<N, true>(b.a, b.map, b.base, b.nscan, b.dispenser);
 }
 
 template <int N>
@@ -666,6 +691,42 @@ int fourier_occupancy(int N, size_t smem) {
   if (!f) return 0;
   if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+static const void* fourier_batch_kernel(int N) {
+  switch (N) {
+    case 16: return (const void*)k_fourier_batch<16>;
+    case 32: return (const void*)k_fourier_batch<32>;
+    case 64: return (const void*)k_fourier_batch<64>;
+    case 128: return (const void*)k_fourier_batch<128>;
+    case 256: return (const void*)k_fourier_batch<256>;
+    default: return nullptr;
+  }
+}
+
+cudaError_t launch_fourier_batch(const FourierBatch& b, int N, int grid, size_t smem, cudaStream_t s) {
+  const void* f = fourier_batch_kernel(N);
+  if (!f) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  switch (N) {
+    case 16: k_fourier_batch<16><<<grid, kThreads, smem, s>>>(b); break;
+    case 32: k_fourier_batch<32><<<grid, kThreads, smem, s>>>(b); break;
+    case 64: k_fourier_batch<64><<<grid, kThreads, smem, s>>>(b); break;
+    case 128: k_fourier_batch<128><<<grid, kThreads, smem, s>>>(b); break;
+    case 256: k_fourier_batch<256><<<grid, kThreads, smem, s>>>(b); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int fourier_batch_occupancy(int N, size_t smem) {
+  const void* f = fourier_batch_kernel(N);
+  if (!f) return 0;
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, smem) != cudaSuccess) return 0;
   return nb;

@@ -2,6 +2,7 @@
 // kernels (dm_fourier.cu, dm_overlap.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -58,6 +59,21 @@ struct FourierArgs {
   int* counters;          // [0] dispenser, then done R/C/I per chunk
   int* status;
 };
+
+// Several scans of one frame size in one persistent Fourier launch: scan s
+// owns tasks [base[s], base[s+1]) of the launch counter; its own plan,
+// counters and scratch ring are in a[s], its scratch tensor map in map[s].
+// The whole table is a kernel parameter (no tensor map in global memory).
+constexpr int kMaxBatchScans = 16;
+struct FourierBatch {
+  CUtensorMap map[kMaxBatchScans];
+  FourierArgs a[kMaxBatchScans];
+  int base[kMaxBatchScans + 1];
+  int nscan;
+  int* dispenser;
+};
+cudaError_t launch_fourier_batch(const FourierBatch& b, int N, int grid, size_t smem, cudaStream_t s);
+int fourier_batch_occupancy(int N, size_t smem);
 
 // ---------------------------------------------------------------------------
 // Object update (Eq. 5): gather over the views that cover each object tile.

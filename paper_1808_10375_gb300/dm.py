@@ -55,7 +55,8 @@ EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_
            "dm_kernel_name", "dm_device_bytes", "dm_free", "dm_last_error", "dm_probe_update_static",
            "dm_object_partials", "dm_object_apply", "dm_probe_partials", "dm_probe_apply",
            "dm_fourier_error_partials", "dm_finish_iteration", "dm_set_graph", "dm_autotune",
-           "dm_get_plan"]
+           "dm_get_plan", "dm_batch_create", "dm_batch_iterate", "dm_batch_set_graph", "dm_batch_free",
+           "dm_batch_last_error"]
 
 _lib = None
 
@@ -102,6 +103,11 @@ def load(path: str = LIB_PATH):
         "dm_set_graph": (ctypes.c_int, [vp, i32]),
         "dm_autotune": (ctypes.c_int, [vp, i32, dp]),
         "dm_get_plan": (ctypes.c_int, [vp, P(i64)]),
+        "dm_batch_create": (ctypes.c_int, [P(vp), P(vp), i32]),
+        "dm_batch_iterate": (ctypes.c_int, [vp, i32]),
+        "dm_batch_set_graph": (ctypes.c_int, [vp, i32]),
+        "dm_batch_free": (None, [vp]),
+        "dm_batch_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -253,6 +259,50 @@ def dm_get_plan(ctx: Context) -> dict:
     _check(load().dm_get_plan(ctx.handle, out), ctx)
     return dict(scratch_bytes=out[0], views_per_chunk=out[1], strips_per_column_task=out[2],
                 strip_buffers=out[3], ctas=out[4])
+
+
+class Batch:
+    """Handle of one dm_batch and the contexts it advances."""
+
+    def __init__(self, handle, ctxs):
+        self.handle = handle
+        self.ctxs = list(ctxs)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().dm_batch_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def _bcheck(rc, batch=None):
+    if rc != DM_OK:
+        msg = load().dm_batch_last_error(batch.handle if batch is not None else None)
+        raise DMError(rc, (msg or b"").decode())
+    return rc
+
+
+def dm_batch_create(ctxs) -> Batch:
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.handle for c in ctxs])
+    h = ctypes.c_void_p()
+    _bcheck(load().dm_batch_create(ctypes.byref(h), arr, len(ctxs)))
+    return Batch(h.value, ctxs)
+
+
+def dm_batch_iterate(batch: Batch, n_iter: int = 1):
+    return _bcheck(load().dm_batch_iterate(batch.handle, int(n_iter)), batch)
+
+
+def dm_batch_set_graph(batch: Batch, enable: bool = True):
+    return _bcheck(load().dm_batch_set_graph(batch.handle, 1 if enable else 0), batch)
+
+
+def dm_batch_free(batch: Batch):
+    if batch.handle:
+        load().dm_batch_free(batch.handle)
+        batch.handle = None
 
 
 def dm_run_step(ctx: Context, step: int):

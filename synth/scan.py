@@ -30,6 +30,29 @@ import math
 
 import numpy as np
 
+# Sixteen scans of uneven size for the batched form: frames 64/128/256,
+# 400 to 6400 views, 1 to 8 probe modes, objects 454 to 1442 px.  Each entry
+# is (n, modes, grid side, step); the object is sized to hold the raster.
+BATCH16 = [
+    (256, 8, 40, 30), (256, 4, 30, 40), (256, 2, 50, 24), (256, 6, 20, 60),
+    (128, 4, 80, 16), (128, 8, 60, 20), (128, 1, 50, 24), (128, 3, 40, 30),
+    (128, 5, 30, 40), (128, 2, 70, 18),
+    (64, 8, 80, 8), (64, 1, 70, 10), (64, 2, 60, 12), (64, 6, 50, 14),
+    (64, 4, 40, 16), (64, 3, 20, 20),
+]
+
+
+def batch16_configs():
+    """Workload dicts of the sixteen-scan batch (seeds 2001..2016)."""
+    out = []
+    for i, (n, modes, g, step) in enumerate(BATCH16):
+        side = (g - 1) * step + n + 10
+        out.append(dict(n=n, modes=modes, grid=(g, g), step=step, jitter=1, obj=(side, side),
+                        probe="gauss" if modes == 1 else "hg", fwhm=n / 2.0,
+                        photons=1e6 if n == 64 else 1e7, seed=2001 + i))
+    return out
+
+
 WORKLOADS = {
     "sm64": dict(n=64, modes=1, grid=(10, 10), step=8, jitter=1,
                  obj=(160, 160), probe="gauss", fwhm=32.0, photons=1e6,
