@@ -289,6 +289,27 @@ int dm_probe_apply(dm_ctx* ctx, const double* num, const double* den, int32_t me
 int dm_fourier_error_partials(dm_ctx* ctx, double* sums);
 int dm_finish_iteration(dm_ctx* ctx, const double* sums);
 
+/* Batched 2-D DFT of complex frames in two precision forms (the paper runs
+ * FP64 and names single precision as future work, Sec. V).  N = 256 only.
+ *   out[f][q] = sum_u in[f][u] exp(-+2 pi i (q . u) / N), unnormalised, '-'
+ *   for the forward transform (inverse != 0 takes '+').
+ * precision DM_DFT_FP32: the FP32 register radix-16 FFT of the Fourier step.
+ * precision DM_DFT_BF16X3: each 16-point stage on the tensor cores as complex
+ *   GEMMs with split BF16 operands (a = hi + lo, three products hi*hi +
+ *   hi*lo + lo*hi per real GEMM) and FP32 accumulation; the twiddles between
+ *   stages in FP32.  Its error is bounded as stated in the tests (relative L2
+ *   against an FP64 DFT).
+ * in, work, out: device pointers on the current device, [frames][N][N]
+ * complex (float pairs); work is caller-owned scratch of the same size and
+ * must alias neither in nor out; out may equal in.  Work is enqueued on
+ * `stream` (a cudaStream_t; NULL is the default stream).  The first call on a
+ * device fills the library's twiddle tables: make it before any stream
+ * capture.  Errors: DM_EINVAL, DM_ECUDA (message in dm_last_error(NULL)). */
+#define DM_DFT_FP32 0
+#define DM_DFT_BF16X3 1
+int dm_dft2(const float* in, float* work, float* out, int32_t n, int32_t frames, int32_t inverse,
+            int32_t precision, void* stream);
+
 /* Release everything the context holds (NULL is ignored). */
 void dm_free(dm_ctx* ctx);
 

@@ -686,11 +686,21 @@ static const void* fourier_kernel(int N) {
   }
 }
 
+// The dynamic shared-memory limit is a property of the kernel, shared by
+// every context that launches it: set it to the device's opt-in maximum so
+// that plans of different sizes can all launch.
+static cudaError_t allow_max_smem(const void* f) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
+  return e;
+}
+
 int fourier_occupancy(int N, size_t smem) {
   const void* f = fourier_kernel(N);
   if (!f) return 0;
-  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
+  if (allow_max_smem(f) != cudaSuccess) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, smem) != cudaSuccess) return 0;
   return nb;
@@ -710,7 +720,7 @@ static const void* fourier_batch_kernel(int N) {
 cudaError_t launch_fourier_batch(const FourierBatch& b, int N, int grid, size_t smem, cudaStream_t s) {
   const void* f = fourier_batch_kernel(N);
   if (!f) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(f);
   if (e != cudaSuccess) return e;
   switch (N) {
     case 16: k_fourier_batch<16><<<grid, kThreads, smem, s>>>(b); break;
@@ -726,7 +736,7 @@ cudaError_t launch_fourier_batch(const FourierBatch& b, int N, int grid, size_t 
 int fourier_batch_occupancy(int N, size_t smem) {
   const void* f = fourier_batch_kernel(N);
   if (!f) return 0;
-  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (allow_max_smem(f) != cudaSuccess) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, smem) != cudaSuccess) return 0;
   return nb;

@@ -178,6 +178,13 @@ cudaError_t launch_metrics(const double* ef_part, long long n_ef, const double* 
                            int* status, cudaStream_t s);
 cudaError_t launch_mode_power(const float2* probe, int N, int M, double* out, cudaStream_t s);
 
+// Batched 2-D DFT of 256 x 256 frames (dm_dft.cu): tables and limits once
+// per device, then the two row passes (precision 0 FP32, 1 split BF16 on the
+// tensor cores).
+cudaError_t prepare_dft256(cudaStream_t s);
+cudaError_t launch_dft256(const float2* in, float2* work, float2* out, int frames, bool inverse, int precision,
+                          cudaStream_t s);
+
 // Message returned by dm_last_error(NULL) (calls made without a context).
 void set_global_error(const char* msg);
 

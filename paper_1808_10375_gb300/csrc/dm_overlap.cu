@@ -517,8 +517,11 @@ cudaError_t launch_obj_source(float2* cview, const float2* psi, const float2* pr
 template <int MAXM, int PX>
 static cudaError_t probe_partial_launch(const ProbePartialArgs& a, int num_sms, cudaStream_t s) {
   const size_t smem = probe_partial_smem_bytes(a.M);
+  // the limit is shared by every context using this instance: allow the
+  // largest mode count the instance serves
   const void* f = (const void*)k_probe_partial<MAXM, PX>;
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)probe_partial_smem_bytes(MAXM));
   if (e != cudaSuccess) return e;
   const int tp = PX * kThreads;
   const int items = ((a.N * a.N + tp - 1) / tp) * a.groups;
@@ -536,13 +539,13 @@ size_t probe_partial_smem_bytes(int M) {
 // modes ahead of any launch (so that no attribute is set while a stream is
 // being captured).
 cudaError_t prepare_probe_partial(int M) {
-  const size_t smem = probe_partial_smem_bytes(M);
+  const int maxm = M <= 1 ? 1 : M <= 2 ? 2 : M <= 4 ? 4 : M <= 8 ? 8 : 16;
   const void* f = M <= 1   ? (const void*)k_probe_partial<1, kProbePxPerThread>
                   : M <= 2 ? (const void*)k_probe_partial<2, kProbePxPerThread>
                   : M <= 4 ? (const void*)k_probe_partial<4, kProbePxPerThread>
                   : M <= 8 ? (const void*)k_probe_partial<8, kProbePxPerThread>
                            : (const void*)k_probe_partial<16, 1>;
-  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)probe_partial_smem_bytes(maxm));
 }
 
 cudaError_t launch_probe_partial(const ProbePartialArgs& a, int num_sms, cudaStream_t s) {

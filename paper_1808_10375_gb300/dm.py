@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libptycho_dm.so")
 DM_OK, DM_EINVAL, DM_ENOMEM, DM_ECUDA, DM_ENONFINITE, DM_ETIMEOUT = 0, -1, -2, -3, -4, -5
 DM_HOST, DM_DEVICE = 0, 1
 DM_STEP_FOURIER, DM_STEP_OBJECT, DM_STEP_PROBE = 0, 1, 2
+DM_DFT_FP32, DM_DFT_BF16X3 = 0, 1
 (DM_KERNEL_FOURIER, DM_KERNEL_OBJECT_GATHER, DM_KERNEL_OBJECT_FINAL, DM_KERNEL_PROBE_PARTIAL,
  DM_KERNEL_PROBE_FINAL, DM_KERNEL_METRICS, DM_KERNEL_OTHER, DM_KERNEL_COUNT) = range(8)
 
@@ -56,7 +57,7 @@ EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_
            "dm_object_partials", "dm_object_apply", "dm_probe_partials", "dm_probe_apply",
            "dm_fourier_error_partials", "dm_finish_iteration", "dm_set_graph", "dm_autotune",
            "dm_get_plan", "dm_batch_create", "dm_batch_iterate", "dm_batch_set_graph", "dm_batch_free",
-           "dm_batch_last_error"]
+           "dm_batch_last_error", "dm_dft2"]
 
 _lib = None
 
@@ -108,6 +109,7 @@ def load(path: str = LIB_PATH):
         "dm_batch_set_graph": (ctypes.c_int, [vp, i32]),
         "dm_batch_free": (None, [vp]),
         "dm_batch_last_error": (ctypes.c_char_p, [vp]),
+        "dm_dft2": (ctypes.c_int, [vp, vp, vp, i32, i32, i32, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -303,6 +305,21 @@ def dm_batch_free(batch: Batch):
     if batch.handle:
         load().dm_batch_free(batch.handle)
         batch.handle = None
+
+
+def dm_dft2(x, work=None, out=None, inverse=False, precision=DM_DFT_FP32, stream=None):
+    """Batched unnormalised 2-D DFT of complex64 CUDA frames [F, 256, 256]."""
+    import torch
+    if not (_is_torch(x) and x.is_cuda and x.dtype == torch.complex64 and x.is_contiguous() and x.dim() == 3):
+        raise ValueError("x must be a contiguous complex64 CUDA tensor [frames, N, N]")
+    work = torch.empty_like(x) if work is None else work
+    out = torch.empty_like(x) if out is None else out
+    s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    rc = load().dm_dft2(x.data_ptr(), work.data_ptr(), out.data_ptr(), x.shape[-1], x.shape[0],
+                        1 if inverse else 0, int(precision), s)
+    if rc != DM_OK:
+        raise DMError(rc, (load().dm_last_error(None) or b"").decode())
+    return out
 
 
 def dm_run_step(ctx: Context, step: int):

@@ -25,7 +25,7 @@ def lib():
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(dm_[a-z_]+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(dm_[a-z0-9_]+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
@@ -44,7 +44,7 @@ def test_library_exports_every_declared_symbol(lib):
     nm = shutil.which("nm")
     if nm:
         out = subprocess.run([nm, "-D", "--defined-only", dm.LIB_PATH], capture_output=True, text=True).stdout
-        exported = set(re.findall(r"\b(dm_[a-z_]+)\b", out))
+        exported = set(re.findall(r"\b(dm_[a-z0-9_]+)\b", out))
         assert set(declared_functions()) <= exported
 
 

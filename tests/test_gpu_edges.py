@@ -55,3 +55,28 @@ def test_every_view_within_bound():
     o = run_oracle(s, p0, o0, psi0)
     for j in range(s.views):
         assert rel_l2(g["psi"][j], o["psi"][j]) <= REL_L2, j
+
+
+def test_contexts_of_one_frame_size_with_different_plans():
+    """Kernel launch limits are shared by all contexts: a context created
+    after another one with a smaller plan must not stop the first from
+    running (the first needs more shared memory per CTA)."""
+    from paper_1808_10375_gb300 import dm
+    from parity_util import case, compare, run_oracle
+    big = case(128, 4, (3, 3), 14, (170, 170), 81)
+    small = case(128, 1, (3, 3), 14, (170, 170), 82, probe="gauss")
+    ctxs = []
+    for s, p0, o0, psi0 in (big, small):
+        h, w = s.obj_shape
+        params = dm.dm_params_default(n=s.n, modes=s.modes, views=s.views, obj_h=h, obj_w=w)
+        c = dm.dm_init(params, s.pos, s.intensities, p0, o0)
+        dm.dm_set_exit_waves(c, psi0)
+        ctxs.append(c)
+    dm.dm_autotune(ctxs[1], sample_views=9)
+    for c in ctxs:
+        dm.dm_iterate(c, 1)
+    for c, (s, p0, o0, psi0) in zip(ctxs, (big, small)):
+        g = dict(psi=dm.dm_get_exit_waves(c), probe=dm.dm_get_probe(c), obj=dm.dm_get_object(c),
+                 metrics=[dm.dm_get_error(c, 0)])
+        dm.dm_free(c)
+        compare(g, run_oracle(s, p0, o0, psi0))
