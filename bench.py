@@ -58,9 +58,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-views", type=int, default=600, help="views in the oracle sample")
-    ap.add_argument("--workload", choices=["mm256", "batch16"], default="mm256",
+    ap.add_argument("--workload", choices=["mm256", "batch16", "dft256"], default="mm256",
                     help="mm256: the 8-mode 256x256 scan (the headline); batch16: sixteen uneven scans "
-                         "advanced as one batch")
+                         "advanced as one batch; dft256: the batched 2-D DFT in both precision forms")
     return ap.parse_args()
 
 
@@ -329,6 +329,75 @@ def run_batch16(args, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_dft256(args, rank, local):
+    """The batched 256 x 256 2-D DFT (dm_dft2) on the exit waves of the first
+    1,000 views of the 8-mode workload (8,000 frames), in the FP32 register-FFT
+    form and the split-BF16 tensor-core form: frames per second, the tensor
+    form's tensor-core FLOP/s against the measured bf16 peak, and each form's
+    relative L2 error against numpy's FP64 FFT on a sample of the frames."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_10375_gb300 import dm
+    from synth import make_scan
+    torch.cuda.set_device(local)
+    views = args.views or 1000
+    s = make_scan(WORKLOAD, backend="torch", device="cuda", views=views)
+    p = torch.from_numpy(s.probe.astype(np.complex64)).cuda()
+    o = torch.from_numpy(s.obj.astype(np.complex64)).cuda()
+    pos = torch.from_numpy(s.pos.astype(np.int64)).cuda()
+    ar = torch.arange(s.n, device="cuda")
+    frames = torch.empty((views * s.modes, s.n, s.n), dtype=torch.complex64, device="cuda")
+    for j0 in range(0, views, 100):
+        j1 = min(views, j0 + 100)
+        rr = pos[j0:j1, 0][:, None, None] + ar[None, :, None]
+        cc = pos[j0:j1, 1][:, None, None] + ar[None, None, :]
+        frames[j0 * s.modes:j1 * s.modes] = (p[None] * o[rr, cc][:, None]).reshape(-1, s.n, s.n)
+    nf = frames.shape[0]
+    work = torch.empty_like(frames)
+    out = torch.empty_like(frames)
+    sample = torch.arange(0, nf, max(1, nf // 48))[:48]
+    ref = np.fft.fft2(frames[sample].cpu().numpy().astype(np.complex128))
+    res = {}
+    for prec, name in ((dm.DM_DFT_FP32, "fp32_fft"), (dm.DM_DFT_BF16X3, "bf16x3_tensor")):
+        for _ in range(args.warmup):
+            dm.dm_dft2(frames, work=work, out=out, precision=prec)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            dm.dm_dft2(frames, work=work, out=out, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / args.steps
+        got = out[sample].cpu().numpy().astype(np.complex128)
+        err = float(np.linalg.norm((got - ref).ravel()) / np.linalg.norm(ref.ravel()))
+        res[name] = {"frames_per_s": nf / sec, "ms_per_batch": 1e3 * sec, "rel_l2_vs_fp64": err,
+                     "hbm_gbs": nf * s.n * s.n * 32 / sec / 1e9}
+    # tensor-core work of the split form: 4 radix-16 stages, each 12
+    # m16n8k16 products per 8 lines of 16 points
+    flops = nf * s.n * s.n * 4 * (12 * 2 * 16 * 8 * 16) / (8 * 16)
+    tc = res["bf16x3_tensor"]
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        bf16_peak = 1900.0
+    tflops = flops / (tc["ms_per_batch"] / 1e3) / 1e12
+    if rank == 0:
+        print(json.dumps({
+            "metric": "frames/s, batched 256x256 2-D DFT", "value": tc["frames_per_s"], "unit": "frames/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "bf16x3 (split operands, fp32 accumulation)", "data": "synthetic",
+            "config": {"workload": f"exit waves of the first {views} views of {WORKLOAD} ({nf} frames)",
+                       "error_sample_frames": int(sample.numel())},
+            "forms": res,
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                         "frac": tflops / bf16_peak, "kernel": "k_dft256_rows_tc (mma.sync m16n8k16 bf16)"},
+        }), flush=True)
+
+
 def make_scan_cfg(cfg):
     from synth import make_scan
     return make_scan(cfg, backend="torch", device="cuda")
@@ -342,6 +411,9 @@ def main():
         return
     if args.workload == "batch16":
         run_batch16(args, rank, local)
+        return
+    if args.workload == "dft256":
+        run_dft256(args, rank, local)
         return
     import torch
     torch.cuda.set_device(local)
