@@ -459,12 +459,12 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
   return (double)ef;
 }
 
-// The persistent task loop over one or more scans of frame size N.  Scan s
+// The persistent task loop over several scans of frame size N.  Scan s
 // owns tasks [base[s], base[s+1]) of the launch's counter `disp`; within a
 // scan the order and dependencies are those of its own plan (stage offsets,
 // per-chunk counters, scratch ring).  A CTA's tasks increase, so it moves
 // through the scans in order.
-template <int N, bool BATCH>
+template <int N>
 __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUtensorMap* maps, const int* base,
                                               int nscan, int* disp) {
   extern __shared__ unsigned char smem_raw[];
@@ -486,7 +486,7 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
     fence_mbar_init();
   }
   Pipe pp = {};
-  const int total = BATCH ? base[nscan] : as[0].total_tasks;
+  const int total = base[nscan];
   int next = 0;
   if (threadIdx.x == 0) next = atomicAdd(disp, 1);
   int st_prev = 0, scan_prev = 0;
@@ -499,14 +499,11 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
     __syncthreads();
     const int gtask = s_task;
     if (gtask >= total) break;
-    int sc = 0;
-    if constexpr (BATCH) {
-      sc = scan_prev;
-      while (base[sc + 1] <= gtask) ++sc;
-      if (sc != scan_prev) { scan_prev = sc; st_prev = 0; }
-    }
+    int sc = scan_prev;
+    while (base[sc + 1] <= gtask) ++sc;
+    if (sc != scan_prev) { scan_prev = sc; st_prev = 0; }
     const FourierArgs& a = as[sc];
-    const int task = BATCH ? gtask - base[sc] : gtask;
+    const int task = gtask - base[sc];
     int* doneR = a.counters + 1;
     int* doneC = doneR + a.nchunks;
     int* doneI = doneC + a.nchunks;
@@ -606,17 +603,148 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
   }
 }
 
-// One scan: its task counter is counters[0].
+// One scan: the same task loop as fourier_tasks, specialised to one scan
+// whose arguments are the kernel's own parameters (which keeps its register
+// allocation lean); its task counter is counters[0].
 template <int N>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_fourier(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ FourierArgs a) {
-  fourier_tasks<N, false>(&a, &tmap, nullptr, 1, a.counters);
+    k_fourier(const __grid_constant__ CUtensorMap tmap, const FourierArgs a) {
+  using C = FCfg<N>;
+  extern __shared__ unsigned char smem_raw[];
+  // 128-byte aligned base (TMA boxes land at 128-byte aligned addresses)
+  float2* tw = reinterpret_cast<float2*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+  float2* work = tw + kTwBytes / sizeof(float2);
+  // row tasks: exchange buffers, then two row buffers per transform (staged
+  // psi and P rows of R; the object-source accumulator of I); column tasks:
+  // the strip buffers, then their intensities
+  float2* stage = work;
+  float2* sbuf = work;
+  float* ibuf = reinterpret_cast<float*>(work + (size_t)a.strip_bufs * a.M * N * kStripW);
+  float* fbuf = ibuf + (size_t)a.strip_bufs * N * kStripW;   // modulus factors of the current strip
+  float* nbuf = fbuf + N * kStripW;                          // norms when the modes take several rounds
+  __shared__ __align__(8) uint64_t bars[kMaxStripBufs];
+  __shared__ int s_task;
+  __shared__ int s_skip;
+  __shared__ double s_red[kThreads / 32];
+  for (int i = threadIdx.x; i < tw_entries<N>(); i += kThreads) tw[i] = a.tw[i];
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < kMaxStripBufs; ++b) mbar_init(&bars[b], 1);
+    fence_mbar_init();
+  }
+  Pipe pp = {};
+
+  int* disp = a.counters;
+  int* doneR = a.counters + 1;
+  int* doneC = doneR + a.nchunks;
+  int* doneI = doneC + a.nchunks;
+  int next = 0;
+  if (threadIdx.x == 0) next = atomicAdd(disp, 1);
+  int st_prev = 0;
+  const size_t slot_elems = (size_t)a.B * a.M * N * N;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_task = next;
+      if (next < a.total_tasks) next = atomicAdd(disp, 1);
+    }
+    __syncthreads();
+    const int task = s_task;
+    if (task >= a.total_tasks) break;
+
+    // Decode (stage, kind, chunk, local index).  A CTA's tasks increase, so
+    // the stage is the previous one or a later one: look at the next stage
+    // before falling back to a binary search.
+    int lo = st_prev;
+    if (__ldg(a.stage_off + lo + 1) <= task) {
+      ++lo;
+      if (__ldg(a.stage_off + lo + 1) <= task) {
+        int hi = a.nstages;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (__ldg(a.stage_off + mid) <= task) lo = mid; else hi = mid;
+        }
+      }
+    }
+    const int st = lo;
+    st_prev = lo;
+    int local = task - __ldg(a.stage_off + st);
+    int kind = -1, c = 0;
+    if (st < a.nchunks) {
+      const int nv = min(a.B, a.J - st * a.B);
+      if (local < nv * a.RB) { kind = 0; c = st; } else local -= nv * a.RB;
+    }
+    if (kind < 0) {
+      const int cc = st - a.lag;
+      if (cc >= 0 && cc < a.nchunks) {
+        const int nv = min(a.B, a.J - cc * a.B);
+        if (local < nv * a.CG) { kind = 1; c = cc; } else local -= nv * a.CG;
+      }
+    }
+    if (kind < 0) { kind = 2; c = st - 2 * a.lag; }
+
+    // Wait for what this task consumes.
+    if (threadIdx.x == 0) {
+      bool ok = true;
+      if (kind == 0) {
+        if (c >= a.nslot) {
+          const int cp = c - a.nslot;
+          ok = spin_wait_geq(doneI + cp, min(a.B, a.J - cp * a.B) * a.RB, a.status);
+        }
+      } else if (kind == 1) {
+        ok = spin_wait_geq(doneR + c, min(a.B, a.J - c * a.B) * a.RB, a.status);
+      } else {
+        ok = spin_wait_geq(doneC + c, min(a.B, a.J - c * a.B) * a.CG, a.status);
+      }
+      s_skip = ok ? 0 : 1;
+    }
+    __syncthreads();
+
+    if (!s_skip) {
+      const int sl = c % a.nslot;
+      float2* slot = a.scratch + (size_t)sl * slot_elems;
+      if (kind == 0) {
+        const int jj = local / a.RB, rb = local % a.RB;
+        row_forward<N>(a, stage, tw, c * a.B + jj, jj, rb, slot);
+      } else if (kind == 1) {
+        const int jj = local / a.CG, sg = local % a.CG;
+        const int j = c * a.B + jj;
+        double ef = column_task<N>(a, &tmap, sbuf, ibuf, fbuf, nbuf, tw, bars, pp, j, (sl * a.B + jj) * a.M, sg);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ef += __shfl_xor_sync(0xffffffffu, ef, o);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = ef;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double tot = 0.0;
+          for (int i = 0; i < kThreads / 32; ++i) tot += s_red[i];
+          a.ef_part[(size_t)j * a.CG + sg] = tot;
+        }
+      } else {
+        const int jj = local / a.RB, rb = local % a.RB;
+        row_inverse<N>(a, stage, tw, c * a.B + jj, jj, rb, slot);
+      }
+    }
+    // Publish the task: the barrier orders every thread's writes before
+    // thread 0's device-scope fence and counter update (a release by one
+    // thread after the barrier covers the whole CTA).
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      bulk_wait<0>();   // TMA stores of the task have landed
+      __threadfence();
+      atomicAdd((kind == 0 ? doneR : kind == 1 ? doneC : doneI) + c, 1);
+    }
+  }
+  // Copies that a timed-out wait left in flight must land before the CTA exits.
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < kMaxStripBufs; ++b)
+      while (pp.done[b] < pp.issued[b]) pipe_drain(pp, bars, b, a.status);
+    bulk_wait<0>();
+  }
 }
 
 // Several scans of the same frame size in one persistent launch.
 template <int N>
 __global__ void __launch_bounds__(kThreads, 2) k_fourier_batch(const __grid_constant__ FourierBatch b) {
-  fourier_tasks<N, true>(b.a, b.map, b.base, b.nscan, b.dispenser);
+  fourier_tasks<N>(b.a, b.map, b.base, b.nscan, b.dispenser);
 }
 
 template <int N>
