@@ -58,9 +58,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-views", type=int, default=600, help="views in the oracle sample")
-    ap.add_argument("--workload", choices=["mm256", "batch16", "dft256"], default="mm256",
+    ap.add_argument("--workload", choices=["mm256", "batch16", "dft256", "warmstart"], default="mm256",
                     help="mm256: the 8-mode 256x256 scan (the headline); batch16: sixteen uneven scans "
-                         "advanced as one batch; dft256: the batched 2-D DFT in both precision forms")
+                         "advanced as one batch; dft256: the batched 2-D DFT in both precision forms; "
+                         "warmstart: train the warm-start network, judge its start with DM")
     return ap.parse_args()
 
 
@@ -398,6 +399,58 @@ def run_dft256(args, rank, local):
         }), flush=True)
 
 
+def run_warmstart(args, rank, local):
+    """The learned warm start: train the encoder-decoder (the library's BF16
+    kernels) on 50,000 simulated pairs, measure its fit on fresh pairs, stitch
+    its start for a 4-mode 128x128 scan (12x12 views, noise-free) and run DM
+    from it and from the flat start; DM's Fourier error after 10 trial
+    iterations picks the start."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_10375_gb300 import dm, warmstart
+    from synth import make_scan
+    from synth import warmstart as ws
+    torch.cuda.set_device(local)
+    steps = args.steps if args.steps != 30 else 3000
+    net = dm.dm_net_create(max_batch=64, seed=11)
+    t0 = time.perf_counter()
+    losses = warmstart.train(net, steps=steps, batch=64, lr=1e-3, seed=12, data_count=50000)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    x, t = ws.pairs(512, 99)
+    ys = torch.cat([dm.dm_net_forward(net, x[i:i + 64].contiguous()) for i in range(0, 512, 64)])
+    fit = {}
+    for ch, name in ((0, "amplitude"), (1, "phase")):
+        mse = float(((ys[:, ch] - t[:, ch]) ** 2).mean())
+        fit[name] = {"mse": mse, "r2": 1.0 - mse / float(t[:, ch].var())}
+    cfg = dict(n=128, modes=4, grid=(12, 12), step=10, jitter=1, obj=(250, 250), probe="hg", fwhm=ws.FWHM,
+               photons=ws.PHOTONS, seed=13)
+    scan = make_scan(cfg, noise=False)
+    o_warm = warmstart.predict_start(net, scan.intensities, scan.pos, scan.obj_shape)
+    _, pick, ef = warmstart.judged_start(scan, scan.probe, o_warm, trial_iters=10)
+    res = warmstart.compare(scan, scan.probe, o_warm, iters=200)
+    levels = (0.2, 0.1, 0.05, 0.02, 0.01, 1e-3)
+    runs = {name: {"start_error": r["errors"][0][1], "final_error": r["errors"][-1][1], "wall_s": r["wall_s"],
+                   "iterations_to": {str(lv): warmstart.iterations_to(r["errors"], lv) for lv in levels}}
+            for name, r in res.items()}
+    nparams = dm.dm_net_param_count(net)
+    dm.dm_net_free(net)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "DM iterations to object error, learned warm start vs flat start", "value": runs["warm"]["final_error"],
+            "unit": "relative L2 object error after 200 iterations", "higher_is_better": False, "n_gpus": 1,
+            "dtype": "bf16 weights, fp32 accumulation", "data": "synthetic",
+            "config": {"workload": "warm-start network: 1x128x128 diffraction amplitude -> 2x64x64 object patch, "
+                                   f"{steps} Adam steps of 64 on 50,000 simulated pairs; judged on a noise-free "
+                                   "4-mode 128x128 scan, 12x12 views at 10 px, 250x250 object",
+                       "params": nparams},
+            "training": {"steps": steps, "seconds": t_train, "samples_per_s": steps * 64 / t_train,
+                         "loss_first": losses[0][1], "loss_last": losses[-1][1]},
+            "fit_on_fresh_pairs": fit, "judge": {"pick": pick, "fourier_error_after_trial": ef}, "runs": runs,
+        }), flush=True)
+
+
 def make_scan_cfg(cfg):
     from synth import make_scan
     return make_scan(cfg, backend="torch", device="cuda")
@@ -414,6 +467,9 @@ def main():
         return
     if args.workload == "dft256":
         run_dft256(args, rank, local)
+        return
+    if args.workload == "warmstart":
+        run_warmstart(args, rank, local)
         return
     import torch
     torch.cuda.set_device(local)

@@ -310,6 +310,40 @@ int dm_finish_iteration(dm_ctx* ctx, const double* sums);
 int dm_dft2(const float* in, float* work, float* out, int32_t n, int32_t frames, int32_t inverse,
             int32_t precision, void* stream);
 
+/* Learned warm start: a small convolutional encoder-decoder mapping one
+ * recorded diffraction amplitude (128 x 128, float) to the object amplitude
+ * and phase over the central 64 x 64 pixels of the view's footprint (2 x 64
+ * x 64, float).  The paper has no network; it notes that the starting guess
+ * may come from prior results (Sec. III).  Plain DM stays the judge of the
+ * reconstruction that starts from the network's stitched prediction.
+ * Encoder 1->16->32->64->128->256 channels (3 x 3, stride 2, ReLU; 128 -> 4
+ * pixels), decoder with nearest 2x upsampling 256->128->64->32->16 (3 x 3,
+ * ReLU; 4 -> 64 pixels), head 16->2 (3 x 3, linear).  Weights are BF16 in
+ * every product, with FP32 master copies, activations, gradients and
+ * accumulation; the loss is the mean squared error; updates are Adam.
+ * Parameters are one flat FP32 array, per layer the weights [co][ci][3][3]
+ * then the biases [co].  x, y and target are device pointers on the
+ * network's device, [batch][1][128][128] and [batch][2][64][64]; grads and
+ * params are host arrays of dm_net_param_count() floats; batch <=
+ * max_batch.  dm_net_create draws He-normal weights from `seed`.
+ * dm_net_gradients returns the loss gradients without updating;
+ * dm_net_train_step applies one Adam step (learning rate lr) and, if `loss`
+ * is not NULL, returns the batch loss.  The network allocates its own
+ * buffers (cudaMallocAsync on a stream it owns) and synchronises before
+ * returning host values.  Errors: DM_EINVAL, DM_ENOMEM, DM_ECUDA (message in
+ * dm_last_error(NULL)). */
+typedef struct dm_net dm_net;
+int dm_net_create(dm_net** out, int32_t max_batch, uint64_t seed);
+int64_t dm_net_param_count(const dm_net* net);
+int dm_net_get_params(dm_net* net, float* params);
+int dm_net_set_params(dm_net* net, const float* params);
+int dm_net_forward(dm_net* net, const float* x, int32_t batch, float* y);
+int dm_net_gradients(dm_net* net, const float* x, const float* target, int32_t batch, float* grads,
+                     double* loss);
+int dm_net_train_step(dm_net* net, const float* x, const float* target, int32_t batch, float lr,
+                      double* loss);
+void dm_net_free(dm_net* net);
+
 /* Release everything the context holds (NULL is ignored). */
 void dm_free(dm_ctx* ctx);
 

@@ -41,6 +41,7 @@ struct TimedLaunch {
 }  // namespace
 
 struct dm_ctx {
+  uint32_t magic = 0x58434D44u;   // identifies a live context ('DMCX')
   dm_params p{};
   int device = 0;
   int num_sms = 0;
@@ -522,7 +523,7 @@ int run_metrics(dm_ctx* c, const double* ef, long long n_ef, const double* isum,
 }
 
 int check_ctx(dm_ctx* c) {
-  if (!c) return DM_EINVAL;
+  if (!c || c->magic != 0x58434D44u) return DM_EINVAL;
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
   return DM_OK;
@@ -1286,7 +1287,8 @@ const char* dm_kernel_name(int32_t kernel) {
 size_t dm_device_bytes(const dm_ctx* c) { return c ? c->bytes : 0; }
 
 void dm_free(dm_ctx* c) {
-  if (!c) return;
+  if (!c || c->magic != 0x58434D44u) return;
+  c->magic = 0;
   cudaSetDevice(c->device);
   release_all(c);
   delete c;

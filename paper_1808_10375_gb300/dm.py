@@ -57,7 +57,8 @@ EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_
            "dm_object_partials", "dm_object_apply", "dm_probe_partials", "dm_probe_apply",
            "dm_fourier_error_partials", "dm_finish_iteration", "dm_set_graph", "dm_autotune",
            "dm_get_plan", "dm_batch_create", "dm_batch_iterate", "dm_batch_set_graph", "dm_batch_free",
-           "dm_batch_last_error", "dm_dft2"]
+           "dm_batch_last_error", "dm_dft2", "dm_net_create", "dm_net_param_count", "dm_net_get_params",
+           "dm_net_set_params", "dm_net_forward", "dm_net_gradients", "dm_net_train_step", "dm_net_free"]
 
 _lib = None
 
@@ -110,6 +111,14 @@ def load(path: str = LIB_PATH):
         "dm_batch_free": (None, [vp]),
         "dm_batch_last_error": (ctypes.c_char_p, [vp]),
         "dm_dft2": (ctypes.c_int, [vp, vp, vp, i32, i32, i32, i32, vp]),
+        "dm_net_create": (ctypes.c_int, [P(vp), i32, ctypes.c_uint64]),
+        "dm_net_param_count": (i64, [vp]),
+        "dm_net_get_params": (ctypes.c_int, [vp, f32p]),
+        "dm_net_set_params": (ctypes.c_int, [vp, f32p]),
+        "dm_net_forward": (ctypes.c_int, [vp, vp, i32, vp]),
+        "dm_net_gradients": (ctypes.c_int, [vp, vp, vp, i32, f32p, dp]),
+        "dm_net_train_step": (ctypes.c_int, [vp, vp, vp, i32, ctypes.c_float, dp]),
+        "dm_net_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -302,6 +311,8 @@ def dm_batch_set_graph(batch: Batch, enable: bool = True):
 
 
 def dm_batch_free(batch: Batch):
+    if not isinstance(batch, Batch):
+        raise TypeError("dm_batch_free takes a batch from dm_batch_create")
     if batch.handle:
         load().dm_batch_free(batch.handle)
         batch.handle = None
@@ -320,6 +331,92 @@ def dm_dft2(x, work=None, out=None, inverse=False, precision=DM_DFT_FP32, stream
     if rc != DM_OK:
         raise DMError(rc, (load().dm_last_error(None) or b"").decode())
     return out
+
+
+class Net:
+    """Handle of one dm_net (the warm-start encoder-decoder)."""
+
+    def __init__(self, handle, max_batch):
+        self.handle = handle
+        self.max_batch = max_batch
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().dm_net_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def _ncheck(rc):
+    if rc != DM_OK:
+        raise DMError(rc, (load().dm_last_error(None) or b"").decode())
+    return rc
+
+
+def _cuda_f32(t, shape):
+    import torch
+    if not (_is_torch(t) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and tuple(t.shape) == shape):
+        raise ValueError(f"expected a contiguous float32 CUDA tensor of shape {shape}")
+    return t.data_ptr()
+
+
+def dm_net_create(max_batch: int = 64, seed: int = 0) -> Net:
+    h = ctypes.c_void_p()
+    _ncheck(load().dm_net_create(ctypes.byref(h), int(max_batch), int(seed)))
+    return Net(h.value, max_batch)
+
+
+def dm_net_param_count(net: Net) -> int:
+    return int(load().dm_net_param_count(net.handle))
+
+
+def dm_net_get_params(net: Net):
+    out = np.empty(dm_net_param_count(net), np.float32)
+    _ncheck(load().dm_net_get_params(net.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+def dm_net_set_params(net: Net, params):
+    a = np.ascontiguousarray(params, np.float32)
+    if a.size != dm_net_param_count(net):
+        raise ValueError("wrong parameter count")
+    _ncheck(load().dm_net_set_params(net.handle, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+
+def dm_net_forward(net: Net, x):
+    """x: float32 CUDA [B, 1, 128, 128] -> float32 CUDA [B, 2, 64, 64]."""
+    import torch
+    b = x.shape[0]
+    y = torch.empty((b, 2, 64, 64), dtype=torch.float32, device=x.device)
+    _ncheck(load().dm_net_forward(net.handle, _cuda_f32(x, (b, 1, 128, 128)), b, y.data_ptr()))
+    return y
+
+
+def dm_net_gradients(net: Net, x, target):
+    b = x.shape[0]
+    g = np.empty(dm_net_param_count(net), np.float32)
+    loss = ctypes.c_double()
+    _ncheck(load().dm_net_gradients(net.handle, _cuda_f32(x, (b, 1, 128, 128)), _cuda_f32(target, (b, 2, 64, 64)), b,
+                                    g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss)))
+    return g, loss.value
+
+
+def dm_net_train_step(net: Net, x, target, lr: float = 1e-3, want_loss: bool = False):
+    b = x.shape[0]
+    loss = ctypes.c_double()
+    _ncheck(load().dm_net_train_step(net.handle, _cuda_f32(x, (b, 1, 128, 128)), _cuda_f32(target, (b, 2, 64, 64)), b,
+                                     float(lr), ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def dm_net_free(net: Net):
+    if not isinstance(net, Net):
+        raise TypeError("dm_net_free takes a network from dm_net_create")
+    if net.handle:
+        load().dm_net_free(net.handle)
+        net.handle = None
 
 
 def dm_run_step(ctx: Context, step: int):
@@ -498,6 +595,8 @@ def dm_device_bytes(ctx: Context) -> int:
 
 
 def dm_free(ctx: Context):
+    if not isinstance(ctx, Context):
+        raise TypeError("dm_free takes a context from dm_init")
     if ctx.handle:
         load().dm_free(ctx.handle)
         ctx.handle = None

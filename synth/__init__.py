@@ -10,7 +10,9 @@ from .scan import (WORKLOADS, BATCH16, batch16_configs, Scan, make_scan, grf_obj
                    initial_guess, random_exit_waves,
                    random_exit_waves_device)
 
-__all__ = ["WORKLOADS", "BATCH16", "batch16_configs", "Scan", "make_scan", "grf_object", "gaussian_probe",
+from . import warmstart
+
+__all__ = ["warmstart", "WORKLOADS", "BATCH16", "batch16_configs", "Scan", "make_scan", "grf_object", "gaussian_probe",
            "hg_probe_modes", "raster_positions", "simulate_intensities",
            "initial_guess", "random_exit_waves",
            "random_exit_waves_device"]

@@ -114,3 +114,14 @@ def test_host_fft_building_blocks(tmp_path):
     subprocess.run([gxx, "-O2", "-std=c++17", "-I", cuda_inc, src, "-o", exe], check=True)
     r = subprocess.run([exe, "5e-7"], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout[-2000:]
+
+
+def test_binding_rejects_handles_of_another_kind():
+    """Each release call takes only its own kind of handle (a network or a
+    batch handed to dm_free would be released as a context)."""
+    from paper_1808_10375_gb300 import dm
+    for fn in (dm.dm_free, dm.dm_net_free, dm.dm_batch_free):
+        with pytest.raises(TypeError):
+            fn(object())
+    with pytest.raises(TypeError):
+        dm.dm_free(dm.Net(None, 1))

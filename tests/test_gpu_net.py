@@ -1,0 +1,76 @@
+"""The warm-start network's CUDA kernels against the FP64 reference
+(oracle/net.py) on the same parameters and inputs, and the learned warm
+start against the flat start, judged by DM.
+
+Bounds: forward output relative L2 <= 1e-5 and parameter gradient relative
+L2 <= 1e-4 (FP32 accumulation against FP64, with the same BF16-rounded
+weights on both sides)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1808_10375_gb300 import build
+    build.build()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def test_forward_and_gradients_match_the_reference():
+    import torch
+    from oracle import net as onet
+    from paper_1808_10375_gb300 import dm
+    from synth import warmstart as ws
+    net = dm.dm_net_create(max_batch=4, seed=5)
+    rng = np.random.default_rng(6)
+    p = (onet.he_params(rng) + 0.01 * rng.standard_normal(onet.param_count())).astype(np.float32)
+    assert dm.dm_net_param_count(net) == p.size
+    dm.dm_net_set_params(net, p)
+    assert np.array_equal(dm.dm_net_get_params(net), p)
+    x, t = ws.pairs(2, 7)
+    y = dm.dm_net_forward(net, x)
+    acts = onet.forward(p.astype(np.float64), x.cpu().numpy().astype(np.float64))
+    err_y = _rel(y.cpu().numpy(), acts[-1])
+    g, loss = dm.dm_net_gradients(net, x, t)
+    ref_loss, ref_g = onet.loss_and_gradients(p.astype(np.float64), x.cpu().numpy().astype(np.float64),
+                                              t.cpu().numpy().astype(np.float64))
+    err_g = _rel(g, ref_g)
+    print(f"forward rel L2 {err_y:.2e}, gradient rel L2 {err_g:.2e}, loss {loss:.6g} vs {ref_loss:.6g}")
+    assert err_y <= 1e-5
+    assert err_g <= 1e-4
+    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    dm.dm_net_free(net)
+
+
+def test_warm_start_is_trained_and_judged_by_dm():
+    """The network trains on simulated pairs with the library's kernels, its
+    stitched start is judged by DM's own Fourier error, and the judged start
+    is never worse than the flat start by more than the trial can tell.  On
+    these random-field objects the network gains nothing (its start error
+    and DM's convergence match the flat start's); the test records the
+    comparison and checks the fallback."""
+    from paper_1808_10375_gb300 import dm, warmstart
+    from synth import make_scan
+    from synth import warmstart as ws
+    net = dm.dm_net_create(max_batch=64, seed=11)
+    losses = warmstart.train(net, steps=1500, batch=64, lr=1e-3, seed=12, data_count=20000)
+    print("loss", losses[0], "->", losses[-1])
+    assert losses[-1][1] < 0.5 * losses[0][1]
+    cfg = dict(n=128, modes=4, grid=(12, 12), step=10, jitter=1, obj=(250, 250), probe="hg", fwhm=ws.FWHM,
+               photons=ws.PHOTONS, seed=13)
+    scan = make_scan(cfg, noise=False)
+    o_warm = warmstart.predict_start(net, scan.intensities, scan.pos, scan.obj_shape)
+    o0, pick, ef = warmstart.judged_start(scan, scan.probe, o_warm, trial_iters=10)
+    res = warmstart.compare(scan, scan.probe, o_warm, iters=60)
+    for name in ("flat", "warm"):
+        e = dict(res[name]["errors"])
+        print(name, "start error", round(e[0], 4), "after 20 / 60 iterations", round(e[20], 4), round(e[60], 4))
+    print("judge:", pick, ef)
+    final = {name: dict(res[name]["errors"])[60] for name in ("flat", "warm")}
+    assert final[pick] <= 1.05 * final["flat"]
+    dm.dm_net_free(net)
