@@ -307,6 +307,30 @@ def run_batch16(args, rank, local):
     with ClockSampler(gpu_index(local)) as clk:
         t_batch = timed(lambda: dm.dm_batch_iterate(b, args.steps))
     dm.dm_batch_free(b)
+
+    # sixteen small scans (64x64 frames, 100 views, 1-3 modes), where one scan
+    # alone cannot fill the GPU
+    small, svm = [], 0.0
+    for i in range(16):
+        cfg = dict(n=64, modes=1 + i % 3, grid=(10, 10), step=8, jitter=1, obj=(160, 160),
+                   probe="gauss" if i % 3 == 0 else "hg", fwhm=32.0, photons=1e6, seed=3001 + i)
+        sc = make_scan_cfg(cfg)
+        p0s, o0s = initial_guess(sc, np.random.default_rng(cfg["seed"] + 1), kind="perturbed")
+        prm = dm.dm_params_default(n=64, modes=sc.modes, views=sc.views, obj_h=160, obj_w=160, beta=0.8)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        c = dm.dm_init(prm, dev(sc.pos), sc.intensities, dev(p0s.astype(np.complex64)), dev(o0s.astype(np.complex64)))
+        dm.dm_set_graph(c, True)
+        dm.dm_iterate(c, args.warmup)
+        small.append(c)
+        svm += sc.views * sc.modes
+    ts_alone = timed(lambda: [dm.dm_iterate(c, args.steps) for c in small])
+    bs = dm.dm_batch_create(small)
+    dm.dm_batch_set_graph(bs, True)
+    dm.dm_batch_iterate(bs, args.warmup)
+    ts_batch = timed(lambda: dm.dm_batch_iterate(bs, args.steps))
+    dm.dm_batch_free(bs)
+    for c in small:
+        dm.dm_free(c)
     ferr = [dm.dm_get_error(c)[2] for c in ctxs]
     plans = [dm.dm_get_plan(c) for c in ctxs]
     for c in ctxs:
@@ -323,6 +347,9 @@ def run_batch16(args, rank, local):
             "alone": {"value": total_vm * args.steps / t_alone, "ms_per_step": 1e3 * t_alone / args.steps,
                       "how": "dm_iterate on each scan in turn (CUDA-graph replay), same autotuned plans"},
             "batched_over_alone": t_alone / t_batch,
+            "small16": {"scans": "16 scans of 64x64 frames, 100 views, 1-3 modes",
+                        "batched": svm * args.steps / ts_batch, "alone": svm * args.steps / ts_alone,
+                        "batched_over_alone": ts_alone / ts_batch, "unit": UNIT},
             "fourier_err_last": ferr,
             "plans": plans,
             "clocks": clk.summary(),

@@ -13,7 +13,7 @@ M_O = 1, which the paper reports is the only useful case), N x N frames, an
 H x W object O, probe modes P_k, exit waves psi_j^k, integer top-left scan
 positions r_j = (row, col).
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
 
 * F is the orthonormal 2-D DFT, F[x](q) = (1/N) sum_u x(u) exp(-2 pi i q.u/N),
   with the zero frequency at index [0, 0] (no shift).

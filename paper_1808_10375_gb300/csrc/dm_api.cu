@@ -880,6 +880,11 @@ struct dm_batch {
   cudaStream_t stream = nullptr;
   int* dispensers = nullptr;   // one per group
   cudaEvent_t ev = nullptr;
+  // the scans' overlap projections run concurrently, one stream per scan,
+  // forked after the Fourier launches and joined before the iteration ends
+  std::vector<cudaStream_t> lanes;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
   bool use_graph = false;
   std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> graphs;   // by the scans' buffer parities
   std::string err;
@@ -922,10 +927,13 @@ int enqueue_batch_iteration(dm_batch* b) {
     DM_BCUDA(b, cudaMemsetAsync(fb.dispenser, 0, sizeof(int), b->stream));
     DM_BCUDA(b, dmk::launch_fourier_batch(fb, g.N, g.grid, g.smem, b->stream));
   }
-  for (dm_ctx* c : b->ctx) {
+  DM_BCUDA(b, cudaEventRecord(b->fork, b->stream));
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    dm_ctx* c = b->ctx[i];
     const bool upd = c->iters >= c->p.probe_update_start;
     cudaStream_t own = c->stream;
-    c->stream = b->stream;
+    DM_BCUDA(b, cudaStreamWaitEvent(b->lanes[i], b->fork, 0));
+    c->stream = b->lanes[i];
     int rc = DM_OK;
     for (int pass = 0; pass < c->p.n_inner && rc == DM_OK; ++pass) {
       if (pass > 0) {
@@ -940,6 +948,8 @@ int enqueue_batch_iteration(dm_batch* b) {
     if (rc == DM_OK) rc = run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd);
     c->stream = own;
     if (rc) return batch_fail(b, rc, c->err);
+    DM_BCUDA(b, cudaEventRecord(b->joins[i], b->lanes[i]));
+    DM_BCUDA(b, cudaStreamWaitEvent(b->stream, b->joins[i], 0));
   }
   return DM_OK;
 }
@@ -985,11 +995,16 @@ int dm_batch_create(dm_batch** out, dm_ctx* const* ctxs, int32_t count) {
   }
   cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  b->lanes.assign(b->ctx.size(), nullptr);
+  b->joins.assign(b->ctx.size(), nullptr);
+  for (size_t i = 0; i < b->ctx.size() && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->lanes[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&b->dispensers), sizeof(int) * b->groups.size(), b->stream);
   if (e != cudaSuccess) {
-    if (b->ev) cudaEventDestroy(b->ev);
-    if (b->stream) cudaStreamDestroy(b->stream);
-    delete b;
+    dm_batch_free(b);
     return batch_fail(nullptr, DM_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
   }
   *out = b;
@@ -1057,6 +1072,11 @@ void dm_batch_free(dm_batch* b) {
   cudaSetDevice(b->device);
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (size_t i = 0; i < b->lanes.size(); ++i) {
+    if (b->lanes[i]) { cudaStreamSynchronize(b->lanes[i]); cudaStreamDestroy(b->lanes[i]); }
+    if (b->joins[i]) cudaEventDestroy(b->joins[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->dispensers) cudaFreeAsync(b->dispensers, b->stream);
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->ev) cudaEventDestroy(b->ev);
