@@ -58,10 +58,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-views", type=int, default=600, help="views in the oracle sample")
-    ap.add_argument("--workload", choices=["mm256", "batch16", "dft256", "warmstart"], default="mm256",
+    ap.add_argument("--workload", choices=["mm256", "batch16", "dft256", "warmstart", "embed"], default="mm256",
                     help="mm256: the 8-mode 256x256 scan (the headline); batch16: sixteen uneven scans "
                          "advanced as one batch; dft256: the batched 2-D DFT in both precision forms; "
-                         "warmstart: train the warm-start network, judge its start with DM")
+                         "warmstart: train the warm-start network, judge its start with DM; embed: the "
+                         "object embedding fused into the exit-wave update against a separate pass")
     return ap.parse_args()
 
 
@@ -478,6 +479,73 @@ def run_warmstart(args, rank, local):
         }), flush=True)
 
 
+def run_embed(args, rank, local):
+    """The object embedding (Eq. 5 numerator, Sec. III) done inside the
+    exit-wave update pass against the same embedding as a pass of its own.
+
+    Fused (dm_iterate): the Fourier-step kernel writes c_j = sum_k conj(P_k)
+    psi_j^k for each view while psi_j is still in registers, and the object
+    gather only sums c_j.  Separate (dm_run_step Fourier, object, probe): the
+    object step first recomputes c_j from the stored exit waves, re-reading
+    all of them.  The paper overlaps the embedding of one batch of views with
+    the exit-wave update of the next and reports about 20 % from it."""
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_10375_gb300 import dm
+    s, p0, o0 = make_inputs(args.views, "cuda")
+    n, m, j = s.n, s.modes, s.views
+    h, w = s.obj_shape
+    params = dm.dm_params_default(n=n, modes=m, views=j, obj_h=h, obj_w=w, beta=0.8)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx = dm.dm_init(params, dev(s.pos), s.intensities, dev(p0), dev(o0), stream=stream.cuda_stream)
+
+    def separate(k):
+        for _ in range(k):
+            dm.dm_run_step(ctx, dm.DM_STEP_FOURIER)
+            dm.dm_run_step(ctx, dm.DM_STEP_OBJECT)
+            dm.dm_run_step(ctx, dm.DM_STEP_PROBE)
+
+    def timed(fn):
+        fn(args.warmup)
+        torch.cuda.synchronize()
+        dm.dm_set_timing(ctx, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kt = {dm.dm_kernel_name(k): dm.dm_get_timing(ctx, k) for k in range(dm.DM_KERNEL_COUNT)}
+        dm.dm_set_timing(ctx, False)
+        per = {k: v[0] / v[1] for k, v in kt.items() if v[1]}
+        return e0.elapsed_time(e1) / args.steps, per
+
+    with ClockSampler(gpu_index(local)) as clk:
+        fused_ms, fused_k = timed(lambda k: dm.dm_iterate(ctx, k))
+        sep_ms, sep_k = timed(separate)
+    dm.dm_free(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": j * m / (fused_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": fused_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": ("embed: " + WORKLOAD_DESC if args.views is None
+                                    else f"embed: {WORKLOAD_DESC} (first {j} views)"),
+                       "l2": "inputs larger than L2"},
+            "fused": {"ms_per_iteration": fused_ms, "kernels_ms": fused_k},
+            "separate": {"ms_per_iteration": sep_ms, "kernels_ms": sep_k,
+                         "value": j * m / (sep_ms / 1e3)},
+            "fused_speedup": sep_ms / fused_ms,
+            "gpu_launches": KERNELS_PER_ITER * args.steps,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def make_scan_cfg(cfg):
     from synth import make_scan
     return make_scan(cfg, backend="torch", device="cuda")
@@ -497,6 +565,9 @@ def main():
         return
     if args.workload == "warmstart":
         run_warmstart(args, rank, local)
+        return
+    if args.workload == "embed":
+        run_embed(args, rank, local)
         return
     import torch
     torch.cuda.set_device(local)
