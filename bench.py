@@ -99,7 +99,15 @@ class ClockSampler:
                                          stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
-        time.sleep(0.3)
+        # Wait (at most 10 s) for the first sample, so that nvidia-smi's own
+        # start-up is over before the timed region begins; that sample is
+        # taken before the region and is left out of the summary.
+        if self.proc is not None:
+            import select
+            ready, _, _ = select.select([self.proc.stdout], [], [], 10.0)
+            if ready:
+                self.proc.stdout.readline()
+        time.sleep(0.05)
         return self
 
     def __exit__(self, *exc):
