@@ -58,11 +58,16 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-views", type=int, default=600, help="views in the oracle sample")
-    ap.add_argument("--workload", choices=["mm256", "batch16", "dft256", "warmstart", "embed"], default="mm256",
+    ap.add_argument("--tte-iters", type=int, default=3000, help="tte: iteration limit of each DM run")
+    ap.add_argument("--tte-train-steps", type=int, default=3000, help="tte: training steps of the warm-start "
+                    "network (0: no warm-started run)")
+    ap.add_argument("--workload", choices=["mm256", "batch16", "dft256", "warmstart", "embed", "tte"],
+                    default="mm256",
                     help="mm256: the 8-mode 256x256 scan (the headline); batch16: sixteen uneven scans "
                          "advanced as one batch; dft256: the batched 2-D DFT in both precision forms; "
                          "warmstart: train the warm-start network, judge its start with DM; embed: the "
-                         "object embedding fused into the exit-wave update against a separate pass")
+                         "object embedding fused into the exit-wave update against a separate pass; tte: "
+                         "time to object error 1e-3 of plain FP32 DM from a flat, a random and a learned start")
     return ap.parse_args()
 
 
@@ -554,6 +559,112 @@ def run_embed(args, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_tte(args, rank, local):
+    """Time to object error 1e-3 of plain FP32 DM on the 4-mode 128x128 scan
+    (2,500 views at 10 px, 640x640 object), simulated without noise so that
+    the reference is the true object.
+
+    Error: relative L2 of the object after the best complex scalar, on the
+    pixels where sum_j sum_k |P_k|^2 reaches 0.1 of its maximum.  The probe
+    is the true one and stays fixed: with the probe free, a linear phase ramp
+    moved from the object to the probe changes no intensity, so the object
+    would be fixed only up to that ramp.  Starts: the flat object, a random
+    object (white amplitude in [0.5, 1] and phase in [-pi/2, pi/2], seeded),
+    and the learned start (the network trained here, stitched, with DM's
+    Fourier error after 10 trial iterations choosing between it and the flat
+    start).  Device seconds are CUDA-event time of the iterations alone; the
+    object is copied back and scored every 10 iterations outside it."""
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_10375_gb300 import dm, warmstart
+    from synth import make_scan
+    from synth import warmstart as ws
+    scan = make_scan("mm128", noise=False)
+    n, m, j = scan.n, scan.modes, scan.views
+    h, w = scan.obj_shape
+    den = np.zeros((h, w))
+    p2 = np.sum(np.abs(scan.probe) ** 2, axis=0)
+    for r, c in scan.pos:
+        den[r:r + n, c:c + n] += p2
+    covered = den >= 0.1 * den.max()
+    rng = np.random.Generator(np.random.PCG64(2002))
+    starts = {"flat": np.ones((h, w), np.complex64),
+              "random": ((0.5 + 0.5 * rng.random((h, w))) *
+                         np.exp(1j * np.pi * (rng.random((h, w)) - 0.5))).astype(np.complex64)}
+    train_info = None
+    if args.tte_train_steps > 0:
+        net = dm.dm_net_create(max_batch=64, seed=11)
+        t0 = time.perf_counter()
+        warmstart.train(net, steps=args.tte_train_steps, batch=64, lr=1e-3, seed=12, data_count=50000)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        o_warm = warmstart.predict_start(net, scan.intensities, scan.pos, scan.obj_shape)
+        chosen, pick, ef = warmstart.judged_start(scan, scan.probe, o_warm, trial_iters=10)
+        t_pick = time.perf_counter() - t0
+        dm.dm_net_free(net)
+        starts["learned"] = chosen
+        train_info = {"steps": args.tte_train_steps, "train_s": t_train, "predict_and_judge_s": t_pick,
+                      "judge_pick": pick, "fourier_error_after_trial": ef,
+                      "predicted_start_error": ws.object_error(o_warm.detach().cpu().numpy(), scan.obj, covered)}
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    levels = (1e-1, 1e-2, 1e-3)
+    block = 10
+    runs = {}
+    with ClockSampler(gpu_index(local)) as clk:
+        for name, o0 in starts.items():
+            params = dm.dm_params_default(n=n, modes=m, views=j, obj_h=h, obj_w=w, beta=0.8,
+                                          probe_update_start=1 << 30)
+            ctx = dm.dm_init(params, scan.pos, scan.intensities, scan.probe.astype(np.complex64), o0,
+                             stream=stream.cuda_stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            dev_s, it, err = 0.0, 0, ws.object_error(o0, scan.obj, covered)
+            first = {}
+            start_err = err
+            t0 = time.perf_counter()
+            while it < args.tte_iters:
+                e0.record(stream)
+                dm.dm_iterate(ctx, block)
+                e1.record(stream)
+                o = dm.dm_get_object(ctx)
+                dev_s += e0.elapsed_time(e1) / 1e3
+                it += block
+                err = ws.object_error(o, scan.obj, covered)
+                for lv in levels:
+                    if err <= lv and str(lv) not in first:
+                        first[str(lv)] = {"iterations": it, "device_s": dev_s, "wall_s": time.perf_counter() - t0}
+                if err <= levels[-1]:
+                    break
+            dm.dm_free(ctx)
+            runs[name] = {"start_error": start_err, "final_error": err, "iterations": it, "device_s": dev_s,
+                          "ms_per_iteration": 1e3 * dev_s / max(it, 1), "to": first}
+    # the FP64 oracle per iteration on the first 100 views of the same scan, scaled to all views
+    from oracle import dm as odm
+    cv = 100
+    psi = odm.init_exit_waves(scan.probe.astype(np.complex128), starts["flat"].astype(np.complex128), scan.pos[:cv])
+    t0 = time.perf_counter()
+    odm.dm_iteration(psi, scan.probe.astype(np.complex128), starts["flat"].astype(np.complex128), scan.pos[:cv],
+                     scan.intensities[:cv].astype(np.float64), update_probe=False)
+    cpu_iter_s = (time.perf_counter() - t0) * j / cv
+    base = runs["random"]["to"].get(str(levels[-1]))
+    if rank == 0:
+        print(json.dumps({
+            "metric": "time to object error 1e-3, plain FP32 DM", "unit": "s",
+            "value": base["device_s"] if base else None, "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "tte: 4-mode difference map, 128x128 frames, 50x50 scan (2,500 views) at 10 px, "
+                                   "640x640 object, noise-free, true probe held fixed, beta 0.8",
+                       "error": "relative L2 after the best complex scalar on pixels with sum |P|^2 >= 0.1 max"},
+            "runs": runs, "learned": train_info, "clocks": clk.summary(),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "s_per_iteration": cpu_iter_s,
+                             "sample": f"one FP64 oracle iteration over the first {cv} views, scaled to {j}"},
+        }), flush=True)
+
+
 def make_scan_cfg(cfg):
     from synth import make_scan
     return make_scan(cfg, backend="torch", device="cuda")
@@ -576,6 +687,9 @@ def main():
         return
     if args.workload == "embed":
         run_embed(args, rank, local)
+        return
+    if args.workload == "tte":
+        run_tte(args, rank, local)
         return
     import torch
     torch.cuda.set_device(local)
