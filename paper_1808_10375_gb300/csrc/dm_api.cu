@@ -270,15 +270,21 @@ int fourier_schedule(dm_ctx* c, int J, const FourierKnobs& k, dmk::FourierArgs& 
   a.lw = 1;
   a.NS = N / a.w;
   const size_t strip_bytes = (size_t)M * N * a.w * sizeof(float2);
-  // Two or three strip buffers while two fit the shared-memory budget (a
-  // third gives a strip and a half of prefetch unless it costs a resident
-  // CTA, checked below), else one.
-  a.strip_bufs = 2 * (strip_bytes + (size_t)N * a.w * sizeof(float)) <= kColumnSmemBudget ? k.max_bufs : 1;
-  a.strip_bufs = std::max(1, std::min(a.strip_bufs, dmk::kMaxStripBufs));
   int spg = 1;
   while (spg * 2 <= a.NS && strip_bytes * spg * 2 <= k.task_bytes) spg *= 2;
   a.SPG = spg;
   a.CG = a.NS / spg;
+  // With fewer modes than column slots, G strips of the task are transformed
+  // together so that G * M of the slots work (G divides SPG).
+  a.G = 1;
+  const int slots = dmk::kThreads / (a.w * R2);
+  while (2 * a.G * M <= slots && 2 * a.G <= a.SPG) a.G *= 2;
+  // Two or three strip buffers while two fit the shared-memory budget (a
+  // third gives a strip and a half of prefetch unless it costs a resident
+  // CTA, checked below), else one.
+  a.strip_bufs =
+      2 * a.G * (strip_bytes + (size_t)N * a.w * sizeof(float)) <= kColumnSmemBudget ? k.max_bufs : 1;
+  a.strip_bufs = std::max(1, std::min(a.strip_bufs, dmk::kMaxStripBufs));
   a.lag = kFourierLag;
   a.nslot = 2 * a.lag + 2;
   const size_t view_bytes = (size_t)M * N * N * sizeof(float2);
@@ -302,10 +308,10 @@ int fourier_schedule(dm_ctx* c, int J, const FourierKnobs& k, dmk::FourierArgs& 
   a.beta = c->p.beta;
   // an extra strip buffer is only worth it while it costs no resident CTA
   while (a.strip_bufs > 1 &&
-         dmk::fourier_occupancy(N, dmk::fourier_smem_bytes(N, M, a.strip_bufs)) <
-             dmk::fourier_occupancy(N, dmk::fourier_smem_bytes(N, M, a.strip_bufs - 1)))
+         dmk::fourier_occupancy(N, dmk::fourier_smem_bytes(N, M, a.strip_bufs, a.G)) <
+             dmk::fourier_occupancy(N, dmk::fourier_smem_bytes(N, M, a.strip_bufs - 1, a.G)))
     --a.strip_bufs;
-  smem = dmk::fourier_smem_bytes(N, M, a.strip_bufs);
+  smem = dmk::fourier_smem_bytes(N, M, a.strip_bufs, a.G);
   const int occ = dmk::fourier_occupancy(N, smem);   // also sets the kernel's shared-memory limit
   if (occ < 1) return fail(c, DM_ECUDA, "Fourier kernel does not fit on an SM");
   grid = std::max(1, std::min(a.total_tasks, occ * c->num_sms));

@@ -230,6 +230,13 @@ struct CCfg {
   static constexpr int TPM = kStripW * R2;     // threads per mode slot
   static constexpr int SLOTS = kThreads / TPM; // modes per round
 };
+
+// Strips a column task transforms at once.  With fewer modes than slots G
+// strips share the slots, strip q of the gang taking slots q*M .. q*M + M - 1.
+// GANG = false compiles the one-strip form (G = 1), which the single-scan
+// kernel uses whenever the modes fill the slots by themselves.
+template <bool GANG>
+__device__ __forceinline__ int col_gang(const FourierArgs& a) { return GANG ? a.G : 1; }
 static_assert(kStripW == 2, "the column-task lane layout assumes two columns per strip");
 
 template <int N>
@@ -311,20 +318,23 @@ __device__ __forceinline__ void col_scale(const float* fb, int t, int c, float2 
     }
 }
 
-// Modulus factor per strip pixel p = q * 2 + c: S = sum_k nrm_k[p], the scale
+// Modulus factor per pixel p = g * 2N + q * 2 + c of the gang's strips
+// (strip g, row q, column c): S = sum_k nrm_{g M + k}[q * 2 + c], the scale
 // s = sqrt(I) / (N sqrt(S)) (0 where S = 0) and f = beta s - 1/N^2 into fb[p];
 // returns this thread's Fourier-error terms added to `ef`.  MM >= M bounds the
 // unrolled mode loop.
-template <int N, int MM>
+template <int N, int MM, bool GANG>
 __device__ __forceinline__ float col_factor(const float* nrm, int nstride, const float* ib, float* fb, int M,
-                                            float beta, float ef) {
+                                            int G, float beta, float ef) {
+  constexpr int SP = N * kStripW;
   const float invN = 1.f / (float)N;
   const float invN2 = invN * invN;
-  for (int p = threadIdx.x; p < N * kStripW; p += kThreads) {
+  for (int p = threadIdx.x; p < G * SP; p += kThreads) {
+    const float* ng = GANG ? nrm + (p / SP) * M * nstride + (p % SP) : nrm + p;
     float S = 0.f;
 #pragma unroll
     for (int k = 0; k < MM; ++k)
-      if (k < M) S += nrm[k * nstride + p];
+      if (k < M) S += ng[k * nstride];
     const float si_ = sqrtf(ib[p]);
     const float ss = sqrtf(S);
     const float sc = (S > 0.f) ? (si_ / ss) * invN : 0.f;
@@ -335,48 +345,55 @@ __device__ __forceinline__ float col_factor(const float* nrm, int nstride, const
   return ef;
 }
 
-template <int N>
+template <int N, bool GANG>
 __device__ __forceinline__ float col_factor_any(const float* nrm, int nstride, const float* ib, float* fb, int M,
-                                                float beta, float ef) {
-  if (M <= 1) return col_factor<N, 1>(nrm, nstride, ib, fb, M, beta, ef);
-  if (M <= 2) return col_factor<N, 2>(nrm, nstride, ib, fb, M, beta, ef);
-  if (M <= 4) return col_factor<N, 4>(nrm, nstride, ib, fb, M, beta, ef);
-  if (M <= 8) return col_factor<N, 8>(nrm, nstride, ib, fb, M, beta, ef);
-  return col_factor<N, kMaxModes>(nrm, nstride, ib, fb, M, beta, ef);
+                                                int G, float beta, float ef) {
+  if (M <= 1) return col_factor<N, 1, GANG>(nrm, nstride, ib, fb, M, G, beta, ef);
+  if (M <= 2) return col_factor<N, 2, GANG>(nrm, nstride, ib, fb, M, G, beta, ef);
+  if (M <= 4) return col_factor<N, 4, GANG>(nrm, nstride, ib, fb, M, G, beta, ef);
+  if (M <= 8) return col_factor<N, 8, GANG>(nrm, nstride, ib, fb, M, G, beta, ef);
+  return col_factor<N, kMaxModes, GANG>(nrm, nstride, ib, fb, M, G, beta, ef);
 }
 
-template <int N>
+template <int N, bool GANG>
 __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtensorMap* tmap, float2* sbuf,
                                               float* ibuf, float* fbuf, float* nbuf, const float2* twF,
                                               uint64_t* bars, Pipe& pp, int j, int zview, int sg) {
   using C = CCfg<N>;
   constexpr int SW = kStripW;
+  constexpr int SP = N * SW;                  // pixels of one strip
   const int M = a.M;
+  const int G = col_gang<GANG>(a);            // strips per buffer (rounds == 1 whenever G > 1)
   const int tid = threadIdx.x;
   const float beta = a.beta;
   const int nbufs = a.strip_bufs;
   const float2* twD = tw_dif<N>(twF);
   const uint32_t strip_elems = (uint32_t)M * N * SW;
+  const uint32_t buf_elems = strip_elems * (uint32_t)G;
   const uint32_t strip_bytes = strip_elems * (uint32_t)sizeof(float2);
   const int slot = tid / C::TPM, c = tid & 1, t = (tid >> 1) & (C::R2 - 1);
+  const int gq = GANG ? slot / M : 0;         // the slot's strip within the gang
   const unsigned mask = slot_mask<N>();
   const int rounds = (M + C::SLOTS - 1) / C::SLOTS;
+  const int nsi = a.SPG / G;                  // gangs of strips in this task
   // norms: in a single round each slot's part of the strip is free once its
   // forward transform is done; otherwise in the separate buffer
   const int nstride = rounds == 1 ? 2 * N * SW : N * SW;   // floats per mode
   float ef = 0.f;  // this thread's few terms; the cross-thread sums are FP64
   const uint64_t pol_first = l2_policy_evict_first(), pol_last = l2_policy_evict_last();
-  auto issue = [&](int si) {  // strip si of the task into buffer si % nbufs (all threads)
-    const int s = sg * a.SPG + si;
+  auto issue = [&](int si) {  // gang si of the task into buffer si % nbufs (all threads)
+    const int s = sg * a.SPG + si * G;
     const int b = si % nbufs;
     if (tid == 0) {
-      mbar_arrive_expect_tx(&bars[b], strip_bytes);
-      tma_load_3d_hint(sbuf + (size_t)b * strip_elems, tmap, s * SW, 0, zview, &bars[b], pol_last);
+      mbar_arrive_expect_tx(&bars[b], strip_bytes * (uint32_t)G);
+      for (int g = 0; g < G; ++g)
+        tma_load_3d_hint(sbuf + (size_t)b * buf_elems + (size_t)g * strip_elems, tmap, (s + g) * SW, 0, zview,
+                         &bars[b], pol_last);
     }
     pp.issued[b]++;
-    const float* ist = a.istrip + ((size_t)j * a.NS + s) * (N * SW);
-    for (int q = tid; q < (N * SW) / 4; q += kThreads)
-      cp_async16_hint(ibuf + b * (N * SW) + 4 * q, ist + 4 * q, pol_first);
+    const float* ist = a.istrip + ((size_t)j * a.NS + s) * SP;   // the gang's strips are consecutive
+    for (int q = tid; q < (G * SP) / 4; q += kThreads)
+      cp_async16_hint(ibuf + b * (G * SP) + 4 * q, ist + 4 * q, pol_first);
     cp_async_commit();
   };
   // Every buffer starts with a strip; later strips are issued in the middle
@@ -385,17 +402,18 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
   // wait for a store on the way between strips.
   if (tid == 0) fence_proxy_async_global();
   int issued = 0;
-  for (; issued < nbufs && issued < a.SPG; ++issued) issue(issued);
-  for (int si = 0; si < a.SPG; ++si) {
-    const int s = sg * a.SPG + si;
+  for (; issued < nbufs && issued < nsi; ++issued) issue(issued);
+  for (int si = 0; si < nsi; ++si) {
+    const int s = sg * a.SPG + si * G;
     const int b = si % nbufs;
-    float2* sb = sbuf + (size_t)b * strip_elems;
-    const float* ib = ibuf + b * (N * SW);
+    float2* sb = sbuf + (size_t)b * buf_elems;
+    const float* ib = ibuf + b * (G * SP);
     pipe_wait(pp, bars, b, a.status);   // every thread waits for the strip itself
     float* nrm = rounds == 1 ? reinterpret_cast<float*>(sb) : nbuf;
     float2 v[C::R1];
     if (rounds == 1) {
-      if (slot < M) {
+      // slot = g * M + k: strip g of the gang, mode k (laid out in that order)
+      if (slot < G * M) {
         float2* base = sb + slot * N * SW + c;
         col_forward<N>(base, t, twF, mask, v);
         __syncwarp(mask);   // the slot's exchange reads are done: its part holds the norms now
@@ -417,18 +435,18 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
     const int later = issued - si - 1;
     if (later >= 2) cp_async_wait<2>(); else if (later == 1) cp_async_wait<1>(); else cp_async_wait<0>();
     __syncthreads();   // A: every mode's norms (and this strip's intensities) are in place
-    if (issued < a.SPG && issued - si < nbufs) {
+    if (issued < nsi && issued - si < nbufs) {
       // strip `issued` goes to the buffer of strip issued - nbufs <= si - 1,
       // whose store was committed before barrier C of that strip
       if (tid == 0) bulk_wait_read<0>();   // at most the store of strip si - 1 is pending
       issue(issued);
       ++issued;
     }
-    ef = col_factor_any<N>(nrm, nstride, ib, fbuf, M, beta, ef);
+    ef = col_factor_any<N, GANG>(nrm, nstride, ib, fbuf, M, G, beta, ef);
     __syncthreads();   // B: the factors are in place; the norms are no longer read
     if (rounds == 1) {
-      if (slot < M) {
-        col_scale<N>(fbuf, t, c, v);
+      if (slot < G * M) {
+        col_scale<N>(fbuf + gq * SP, t, c, v);
         col_inverse<N>(sb + slot * N * SW + c, t, twD, mask, v);
       }
     } else {
@@ -446,10 +464,10 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
     fence_proxy_async_smem();
     __syncthreads();   // C: U of every mode is in the strip
     if (tid == 0) {
-      tma_store_3d_hint(tmap, s * SW, 0, zview, sb, pol_last);
+      for (int g = 0; g < G; ++g) tma_store_3d_hint(tmap, (s + g) * SW, 0, zview, sb + (size_t)g * strip_elems, pol_last);
       bulk_commit();
     }
-    if (nbufs == 1 && issued < a.SPG) {
+    if (nbufs == 1 && issued < nsi) {
       // a single buffer: the next strip waits for this store to leave it
       if (tid == 0) bulk_wait_read<0>();
       issue(issued);
@@ -566,10 +584,11 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
       } else if (kind == 1) {
         const int jj = local / a.CG, sg = local % a.CG;
         const int j = c * a.B + jj;
-        float* ibuf = reinterpret_cast<float*>(work + (size_t)a.strip_bufs * a.M * N * kStripW);
-        float* fbuf = ibuf + (size_t)a.strip_bufs * N * kStripW;   // modulus factors of the current strip
-        float* nbuf = fbuf + N * kStripW;                          // norms when the modes take several rounds
-        double ef = column_task<N>(a, maps + sc, sbuf, ibuf, fbuf, nbuf, tw, bars, pp, j, (sl * a.B + jj) * a.M,
+        const int G = col_gang<true>(a);
+        float* ibuf = reinterpret_cast<float*>(work + (size_t)a.strip_bufs * G * a.M * N * kStripW);
+        float* fbuf = ibuf + (size_t)a.strip_bufs * G * N * kStripW;   // modulus factors of the current gang
+        float* nbuf = fbuf + N * kStripW;                              // norms when the modes take several rounds
+        double ef = column_task<N, true>(a, maps + sc, sbuf, ibuf, fbuf, nbuf, tw, bars, pp, j, (sl * a.B + jj) * a.M,
                                    sg);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ef += __shfl_xor_sync(0xffffffffu, ef, o);
@@ -606,7 +625,7 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
 // One scan: the same task loop as fourier_tasks, specialised to one scan
 // whose arguments are the kernel's own parameters (which keeps its register
 // allocation lean); its task counter is counters[0].
-template <int N>
+template <int N, bool GANG>
 __global__ void __launch_bounds__(kThreads, 2)
     k_fourier(const __grid_constant__ CUtensorMap tmap, const FourierArgs a) {
   using C = FCfg<N>;
@@ -619,9 +638,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   // the strip buffers, then their intensities
   float2* stage = work;
   float2* sbuf = work;
-  float* ibuf = reinterpret_cast<float*>(work + (size_t)a.strip_bufs * a.M * N * kStripW);
-  float* fbuf = ibuf + (size_t)a.strip_bufs * N * kStripW;   // modulus factors of the current strip
-  float* nbuf = fbuf + N * kStripW;                          // norms when the modes take several rounds
+  const int G = col_gang<GANG>(a);
+  float* ibuf = reinterpret_cast<float*>(work + (size_t)a.strip_bufs * G * a.M * N * kStripW);
+  float* fbuf = ibuf + (size_t)a.strip_bufs * G * N * kStripW;   // modulus factors of the current gang
+  float* nbuf = fbuf + N * kStripW;                              // norms when the modes take several rounds
   __shared__ __align__(8) uint64_t bars[kMaxStripBufs];
   __shared__ int s_task;
   __shared__ int s_skip;
@@ -708,7 +728,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       } else if (kind == 1) {
         const int jj = local / a.CG, sg = local % a.CG;
         const int j = c * a.B + jj;
-        double ef = column_task<N>(a, &tmap, sbuf, ibuf, fbuf, nbuf, tw, bars, pp, j, (sl * a.B + jj) * a.M, sg);
+        double ef = column_task<N, GANG>(a, &tmap, sbuf, ibuf, fbuf, nbuf, tw, bars, pp, j, (sl * a.B + jj) * a.M, sg);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ef += __shfl_xor_sync(0xffffffffu, ef, o);
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = ef;
@@ -780,36 +800,38 @@ int fourier_r2(int N) {
 }
 
 template <int N>
-static size_t smem_for(int M, int bufs) {
+static size_t smem_for(int M, int bufs, int G) {
   using C = FCfg<N>;
   static_assert(tw_entries<N>() * sizeof(float2) <= kTwBytes, "twiddle tables exceed their shared area");
   const size_t rows = sizeof(float2) * (size_t)C::GR * 3 * N;   // three row buffers per transform
   const bool multi = M > CCfg<N>::SLOTS;
-  const size_t cols = sizeof(float2) * (size_t)bufs * M * N * kStripW      // strips
-                      + sizeof(float) * (size_t)bufs * N * kStripW         // their intensities
-                      + sizeof(float) * (size_t)N * kStripW                // modulus factors
+  const size_t cols = sizeof(float2) * (size_t)bufs * G * M * N * kStripW  // strips
+                      + sizeof(float) * (size_t)bufs * G * N * kStripW     // their intensities
+                      + sizeof(float) * (size_t)G * N * kStripW            // modulus factors
                       + (multi ? sizeof(float) * (size_t)M * N * kStripW : 0);  // norms (several rounds)
   return 128 + kTwBytes + (rows > cols ? rows : cols);
 }
 
-size_t fourier_smem_bytes(int N, int M, int bufs) {
+size_t fourier_smem_bytes(int N, int M, int bufs, int G) {
   switch (N) {
-    case 16: return smem_for<16>(M, bufs);
-    case 32: return smem_for<32>(M, bufs);
-    case 64: return smem_for<64>(M, bufs);
-    case 128: return smem_for<128>(M, bufs);
-    case 256: return smem_for<256>(M, bufs);
+    case 16: return smem_for<16>(M, bufs, G);
+    case 32: return smem_for<32>(M, bufs, G);
+    case 64: return smem_for<64>(M, bufs, G);
+    case 128: return smem_for<128>(M, bufs, G);
+    case 256: return smem_for<256>(M, bufs, G);
     default: return 0;
   }
 }
 
-static const void* fourier_kernel(int N) {
+// The single-scan kernel: the gang form for every frame size, and for
+// N = 256 also the one-strip form (the modes fill the slots by themselves).
+static const void* fourier_kernel(int N, bool gang) {
   switch (N) {
-    case 16: return (const void*)k_fourier<16>;
-    case 32: return (const void*)k_fourier<32>;
-    case 64: return (const void*)k_fourier<64>;
-    case 128: return (const void*)k_fourier<128>;
-    case 256: return (const void*)k_fourier<256>;
+    case 16: return (const void*)k_fourier<16, true>;
+    case 32: return (const void*)k_fourier<32, true>;
+    case 64: return (const void*)k_fourier<64, true>;
+    case 128: return (const void*)k_fourier<128, true>;
+    case 256: return gang ? (const void*)k_fourier<256, true> : (const void*)k_fourier<256, false>;
     default: return nullptr;
   }
 }
@@ -825,13 +847,19 @@ static cudaError_t allow_max_smem(const void* f) {
   return e;
 }
 
+// Resident CTAs per SM of the single-scan kernel (the smaller of its two
+// forms), with both forms' shared-memory limits set.
 int fourier_occupancy(int N, size_t smem) {
-  const void* f = fourier_kernel(N);
-  if (!f) return 0;
-  if (allow_max_smem(f) != cudaSuccess) return 0;
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, smem) != cudaSuccess) return 0;
-  return nb;
+  int best = -1;
+  for (bool gang : {true, false}) {
+    const void* f = fourier_kernel(N, gang);
+    if (!f) return 0;
+    if (allow_max_smem(f) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, smem) != cudaSuccess) return 0;
+    best = best < 0 ? nb : (nb < best ? nb : best);
+  }
+  return best;
 }
 
 static const void* fourier_batch_kernel(int N) {
@@ -873,11 +901,14 @@ int fourier_batch_occupancy(int N, size_t smem) {
 cudaError_t launch_fourier(const void* tmap, const FourierArgs& a, int grid, size_t smem, cudaStream_t s) {
   const CUtensorMap& m = *static_cast<const CUtensorMap*>(tmap);
   switch (a.N) {
-    case 16: k_fourier<16><<<grid, kThreads, smem, s>>>(m, a); break;
-    case 32: k_fourier<32><<<grid, kThreads, smem, s>>>(m, a); break;
-    case 64: k_fourier<64><<<grid, kThreads, smem, s>>>(m, a); break;
-    case 128: k_fourier<128><<<grid, kThreads, smem, s>>>(m, a); break;
-    case 256: k_fourier<256><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 16: k_fourier<16, true><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 32: k_fourier<32, true><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 64: k_fourier<64, true><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 128: k_fourier<128, true><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 256:
+      if (a.G > 1) k_fourier<256, true><<<grid, kThreads, smem, s>>>(m, a);
+      else k_fourier<256, false><<<grid, kThreads, smem, s>>>(m, a);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -54,6 +54,8 @@ struct FourierArgs {
   int w, lw;              // strip width (columns, = kStripW) and its log2
   int NS;                 // strips per view = N / w
   int strip_bufs;         // strip buffers of a column task (1 to kMaxStripBufs)
+  int G;                  // strips a column task transforms at once (1 when the modes fill
+                          // every slot): G * M slots busy out of kThreads / (w R2)
   int nstages, total_tasks;
   const int* stage_off;   // [nstages + 1] first task of each stage
   int* counters;          // [0] dispenser, then done R/C/I per chunk
@@ -138,7 +140,7 @@ struct ProbeFinalArgs {
 
 // Launchers (return the launch error).
 cudaError_t launch_fourier(const void* tmap, const FourierArgs& a, int grid, size_t smem, cudaStream_t s);
-size_t fourier_smem_bytes(int N, int M, int bufs);
+size_t fourier_smem_bytes(int N, int M, int bufs, int G);
 int fourier_occupancy(int N, size_t smem);
 int fourier_r2(int N);
 // Twiddle tables of the Fourier kernel for frame size N (entries written to

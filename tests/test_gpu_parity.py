@@ -29,6 +29,9 @@ CASES = {
     "n128_m4": (128, 4, (5, 6), 12, (200, 210), 14),
     "n256_m8": (256, 8, (3, 3), 18, (320, 330), 15),
     "n256_m3": (256, 3, (2, 3), 30, (300, 330), 16),
+    # fewer modes than column slots: several strips transformed together
+    "n256_m1": (256, 1, (2, 2), 40, (300, 300), 17),
+    "n128_m2": (128, 2, (3, 3), 20, (170, 180), 18),
 }
 
 
