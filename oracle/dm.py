@@ -219,7 +219,11 @@ def dm_iteration(psi, probe, obj, pos, intensities, beta=0.8, delta_rel=1e-6,
     """Eq. 3, then (Eq. 5, Eq. 4) x n_inner, then Eq. 6.
 
     All inputs are left untouched.  Returns (psi, probe, obj, metrics) with
-    metrics = {"eps_obj", "eps_probe" (list over modes), "fourier_err"}."""
+    metrics = {"eps_obj", "eps_probe" (list over modes), "fourier_err",
+    "eps_psi"}.  eps_psi is the relative change of the exit waves over the
+    whole scan, sqrt(sum |psi_new - psi|^2 / sum |psi_new|^2), the reading
+    taken here of the "psi error" whose estimation Sec. III counts among the
+    costly CPU steps without defining it."""
     psi = np.asarray(psi, dtype=np.complex128)
     probe = np.asarray(probe, dtype=np.complex128)
     obj = np.asarray(obj, dtype=np.complex128)
@@ -234,6 +238,7 @@ def dm_iteration(psi, probe, obj, pos, intensities, beta=0.8, delta_rel=1e-6,
         "eps_obj": rel_change(o_new, obj),
         "eps_probe": [rel_change(p_new[k], probe[k]) for k in range(probe.shape[0])],
         "fourier_err": ef,
+        "eps_psi": rel_change(psi_new, psi),
     }
     return psi_new, p_new, o_new, metrics
 

@@ -7,8 +7,10 @@
   and an extra all-zero mode stays zero and changes nothing;
 * brute force: an independent loop-by-loop implementation written from the
   equations (explicit DFT sums) on tiny inputs, single- and multi-mode;
-* metrics: Eq. 6 on a known perturbation, and the Fourier error on data
-  that is exactly four times the model intensity;
+* metrics: Eq. 6 on a known perturbation, the Fourier error on data that is
+  exactly four times the model intensity, and the exit-wave change (with the
+  exit-wave update itself) on data equal to one or four times the model
+  intensity, where Eq. 3 has a closed form;
 * convergence: a noise-free scan reconstructs the true object (up to a
   complex scalar) to 1e-3 on well-covered pixels.
 """
@@ -240,3 +242,27 @@ def test_noise_free_scan_converges_to_true_object():
             break
     assert errs[-1] < 1e-3, (len(errs), errs[-1])
     assert errs[-1] < 0.01 * errs[0]
+
+
+@pytest.mark.parametrize("scale", [1.0, 4.0])
+def test_exit_wave_change_closed_form(scale):
+    # Data equal to `scale` times the mode sum S of Phi = 2PO - psi makes the
+    # modulus projection a plain factor sqrt(scale) on every mode, so Eq. 3
+    # gives psi' = psi + beta (sqrt(scale) Phi - PO) in closed form, and the
+    # exit-wave change is |psi' - psi| / |psi'| over the whole scan.
+    rng = np.random.default_rng(37)
+    psi, probe, obj, pos, _ = generic_inputs(rng, m=2)
+    n = probe.shape[-1]
+    beta = 0.7
+    inten, want = [], []
+    for j, (r, c) in enumerate(pos):
+        po = probe * obj[None, r:r + n, c:c + n]
+        phi = 2 * po - psi[j]
+        s = sum(np.abs(np.array(_dft(phi[k].tolist(), -1))) ** 2 for k in range(phi.shape[0]))
+        inten.append(scale * s)
+        want.append(psi[j] + beta * (math.sqrt(scale) * phi - po))
+    want = np.array(want)
+    psi_new, _, _, m = dm.dm_iteration(psi, probe, obj, pos, np.array(inten), beta=beta)
+    assert np.abs(psi_new - want).max() <= 1e-12 * np.abs(want).max()
+    d = np.sqrt(np.sum(np.abs(want - psi) ** 2) / np.sum(np.abs(want) ** 2))
+    assert m["eps_psi"] == pytest.approx(d, rel=1e-12)
