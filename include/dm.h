@@ -146,6 +146,21 @@ int dm_set_probe(dm_ctx* ctx, const float* in, int32_t mem_kind);
 int dm_get_error(dm_ctx* ctx, int32_t iter, double* eps_obj, double* eps_probe,
                  double* fourier_err);
 
+/* Exit-wave change eps_psi = sqrt(sum |psi' - psi|^2 / sum |psi'|^2) over
+ * all views, modes and pixels of an iteration: the reading taken here of the
+ * "psi error" that Sec. III counts among the costly steps without defining
+ * it.  The Fourier step computes it only while tracking is on, because it
+ * must read the old exit waves back (8 M N^2 more bytes per view and
+ * iteration); it is off after dm_init.  dm_set_psi_error(ctx, 1) turns it on
+ * (the first call allocates at most 256 bytes per view), 0 off; it
+ * synchronises.
+ * dm_get_psi_error reads iteration `iter` (0-based, -1 = the last; the last
+ * 1024 are kept) into *eps_psi (host): NaN for an iteration that did not
+ * track it (tracking off, a dm_batch iteration, or a sharded iteration);
+ * synchronises. */
+int dm_set_psi_error(dm_ctx* ctx, int32_t enable);
+int dm_get_psi_error(dm_ctx* ctx, int32_t iter, double* eps_psi);
+
 /* Number of completed dm_iterate iterations. */
 int64_t dm_iterations_done(const dm_ctx* ctx);
 

@@ -73,6 +73,8 @@ struct dm_ctx {
   unsigned* dmax_O = nullptr;
   unsigned long long* dmax_P = nullptr;
   double* ef_part = nullptr;
+  double* psi_part = nullptr;   // [J][RB][2] exit-wave change sums (allocated when tracking is on)
+  bool psi_err = false;         // track the exit-wave change eps_psi
   double* isum_part = nullptr;
   double* isum = nullptr;
   double* obj_part = nullptr;
@@ -362,6 +364,7 @@ int plan_fourier(dm_ctx* c, const FourierKnobs& k) {
   a.psi = c->psi; a.istrip = c->istrip; a.pos = c->pos; a.cview = c->cview;
   a.scratch = c->scratch; a.ef_part = c->ef_part; a.tw = c->tw;
   a.stage_off = c->stage_off; a.counters = c->counters; a.status = c->status;
+  a.psi_part = c->psi_err ? c->psi_part : nullptr;
   c->knobs = k;
   return DM_OK;
 }
@@ -520,10 +523,14 @@ int run_probe(dm_ctx* c, const float2* o) {
   return run_probe_div(c);
 }
 
-int run_metrics(dm_ctx* c, const double* ef, long long n_ef, const double* isum, bool upd) {
+// Eq. 6 and the Fourier error into the metrics ring; `psi` when this
+// iteration's Fourier step wrote the exit-wave change sums.
+int run_metrics(dm_ctx* c, const double* ef, long long n_ef, const double* isum, bool upd, bool psi) {
   Timed t(c, DM_KERNEL_METRICS);
+  const bool track = psi && c->fa.psi_part;
   DM_CUDA(c, dmk::launch_metrics(ef, n_ef, isum, c->obj_part, c->obj_final_blocks, c->probe_part,
-                                 c->probe_final_blocks, c->M, upd ? 1 : 0, c->ring, c->iter_dev, c->status,
+                                 c->probe_final_blocks, c->M, upd ? 1 : 0, track ? c->fa.psi_part : nullptr,
+                                 track ? (long long)c->J * c->fa.RB : 0, c->ring, c->iter_dev, c->status,
                                  c->stream));
   return DM_OK;
 }
@@ -637,13 +644,13 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   DM_TRY(alloc_n(c, &c->tw, (size_t)ntw));
   DM_TRY(alloc_n(c, &c->status, 1));
   DM_TRY(alloc_n(c, &c->isum, 1));
-  DM_TRY(alloc_n(c, &c->ring, (size_t)dmk::kMetricsRing * (2 + dmk::kMaxModes)));
+  DM_TRY(alloc_n(c, &c->ring, (size_t)dmk::kMetricsRing * dmk::kRingRow));
   DM_TRY(alloc_n(c, &c->mode_pow, (size_t)M));
   DM_TRY(alloc_n(c, &c->ef_tot, 2));
   DM_TRY(alloc_n(c, &c->iter_dev, 1));
   if ((e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream)) != cudaSuccess) { cuda_fail(c, e, "memset"); return bail(DM_ECUDA); }
   if ((e = cudaMemsetAsync(c->iter_dev, 0, sizeof(long long), c->stream)) != cudaSuccess) { cuda_fail(c, e, "memset"); return bail(DM_ECUDA); }
-  if ((e = cudaMemsetAsync(c->ring, 0, sizeof(double) * dmk::kMetricsRing * (2 + dmk::kMaxModes), c->stream)) != cudaSuccess) {
+  if ((e = cudaMemsetAsync(c->ring, 0, sizeof(double) * dmk::kMetricsRing * dmk::kRingRow, c->stream)) != cudaSuccess) {
     cuda_fail(c, e, "memset"); return bail(DM_ECUDA);
   }
 
@@ -712,7 +719,7 @@ int enqueue_iteration(dm_ctx* c, bool upd) {
     if (!upd) break;  // later passes would repeat the same object update
     if ((rc = run_probe(c, c->obj[c->cur_O ^ 1]))) return rc;
   }
-  return run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd);
+  return run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd, true);
 }
 
 // The iteration for the current (object, probe) buffers as an instantiated
@@ -951,7 +958,7 @@ int enqueue_batch_iteration(dm_batch* b) {
       if (!upd) break;
       if (rc == DM_OK) rc = run_probe(c, c->obj[c->cur_O ^ 1]);
     }
-    if (rc == DM_OK) rc = run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd);
+    if (rc == DM_OK) rc = run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd, false);
     c->stream = own;
     if (rc) return batch_fail(b, rc, c->err);
     DM_BCUDA(b, cudaEventRecord(b->joins[i], b->lanes[i]));
@@ -1190,7 +1197,7 @@ int dm_finish_iteration(dm_ctx* c, const double* sums) {
   if (rc) return rc;
   if (!sums) return fail(c, DM_EINVAL, "sums is NULL");
   if ((rc = copy_in(c, c->ef_tot, sums, 2 * sizeof(double), DM_HOST))) return rc;
-  if ((rc = run_metrics(c, c->ef_tot, 1, c->ef_tot + 1, true))) return rc;
+  if ((rc = run_metrics(c, c->ef_tot, 1, c->ef_tot + 1, true, false))) return rc;
   c->iters++;
   DM_CUDA(c, cudaStreamSynchronize(c->stream));
   return DM_OK;
@@ -1257,13 +1264,40 @@ int dm_get_error(dm_ctx* c, int32_t iter, double* eps_obj, double* eps_probe, do
     return fail(c, DM_EINVAL, "iteration not available");
   double row[2 + dmk::kMaxModes];
   const size_t bytes = sizeof(double) * (2 + c->M);
-  DM_CUDA(c, cudaMemcpyAsync(row, c->ring + (size_t)(it % dmk::kMetricsRing) * (2 + dmk::kMaxModes), bytes,
+  DM_CUDA(c, cudaMemcpyAsync(row, c->ring + (size_t)(it % dmk::kMetricsRing) * dmk::kRingRow, bytes,
                              cudaMemcpyDeviceToHost, c->stream));
   if ((rc = check_status(c))) return rc;
   if (eps_obj) *eps_obj = row[0];
   if (fourier_err) *fourier_err = row[1];
   if (eps_probe) for (int k = 0; k < c->M; ++k) eps_probe[k] = row[2 + k];
   return DM_OK;
+}
+
+int dm_set_psi_error(dm_ctx* c, int32_t enable) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));   // no captured iteration is in flight below
+  if (enable && !c->psi_part && (rc = alloc_n(c, &c->psi_part, (size_t)c->J * c->fa.RB * 2))) return rc;
+  c->psi_err = enable != 0;
+  c->fa.psi_part = c->psi_err ? c->psi_part : nullptr;
+  // captured iterations hold the previous Fourier-step instance
+  for (auto& row : c->gexec)
+    for (auto& g : row)
+      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  return DM_OK;
+}
+
+int dm_get_psi_error(dm_ctx* c, int32_t iter, double* eps_psi) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!eps_psi) return fail(c, DM_EINVAL, "eps_psi is NULL");
+  if (c->iters == 0) return fail(c, DM_EINVAL, "no iteration has run");
+  const int64_t it = iter < 0 ? c->iters - 1 : iter;
+  if (it >= c->iters || it < c->iters - dmk::kMetricsRing || it < 0)
+    return fail(c, DM_EINVAL, "iteration not available");
+  DM_CUDA(c, cudaMemcpyAsync(eps_psi, c->ring + (size_t)(it % dmk::kMetricsRing) * dmk::kRingRow + dmk::kRingPsi,
+                             sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return check_status(c);
 }
 
 int64_t dm_iterations_done(const dm_ctx* c) { return c ? c->iters : -1; }

@@ -112,13 +112,16 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* stage,
 // P once the current epilogue has used its own.  The object-source sum over
 // the modes stays in registers (each thread owns the same positions for every
 // mode).  Pending copy groups at the top of mode k: U_k (with the object row
-// at k = 0), then P_k.
-template <int N>
-__device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* stage, const float2* twF,
-                                            int j, int jj, int rb, const float2* slot) {
+// at k = 0), then P_k.  With PSIERR the old exit waves are read back before
+// they are overwritten, and the thread's sums of |psi' - psi|^2 and |psi'|^2
+// are returned (zero otherwise).
+template <int N, bool PSIERR>
+__device__ __forceinline__ float2 row_inverse(const FourierArgs& a, float2* stage, const float2* twF,
+                                              int j, int jj, int rb, const float2* slot) {
   using C = FCfg<N>;
   const int g = threadIdx.x / C::R2, t = threadIdx.x % C::R2;
-  if (g >= C::GR) return;
+  float2 perr = make_float2(0.f, 0.f);
+  if (g >= C::GR) return perr;
   const int y = rb * C::GR + g;
   const int2 p = a.pos[j];
   const float2* orow = a.obj + (size_t)(p.x + y) * a.W + p.y;
@@ -171,6 +174,12 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* stage,
         const float2 po = cmul(pk, orow_s[x]);
         const float2 g2 = v[p2_index<N>(d, k2)];
         const float2 pn = make_float2(fmaf(c2b, po.x, g2.x), fmaf(c2b, po.y, g2.y));
+        if constexpr (PSIERR) {
+          const float2 old = __ldcs(srow + x);
+          const float2 dv = csub(pn, old);
+          perr.x += cnorm(dv);
+          perr.y += cnorm(pn);
+        }
         __stcs(srow + x, pn);
         const float2 cn = cconjmul(pk, pn);
         cacc[d * C::R2 + k2] = k == 0 ? cn : cadd(cacc[d * C::R2 + k2], cn);
@@ -184,6 +193,7 @@ __device__ __forceinline__ void row_inverse(const FourierArgs& a, float2* stage,
   for (int d = 0; d < C::D; ++d)
 #pragma unroll
     for (int k2 = 0; k2 < C::R2; ++k2) __stcs(crow + t + C::R2 * d + C::R1 * k2, cacc[d * C::R2 + k2]);
+  return perr;
 }
 
 struct Pipe {                     // per-thread bookkeeping of the strip barriers
@@ -601,7 +611,7 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
         }
       } else {
         const int jj = local / a.RB, rb = local % a.RB;
-        row_inverse<N>(a, stage, tw, c * a.B + jj, jj, rb, slot);
+        row_inverse<N, false>(a, stage, tw, c * a.B + jj, jj, rb, slot);
       }
     }
     // Publish the task: the barrier orders every thread's writes before
@@ -625,7 +635,7 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
 // One scan: the same task loop as fourier_tasks, specialised to one scan
 // whose arguments are the kernel's own parameters (which keeps its register
 // allocation lean); its task counter is counters[0].
-template <int N, bool GANG>
+template <int N, bool GANG, bool PSIERR>
 __global__ void __launch_bounds__(kThreads, 2)
     k_fourier(const __grid_constant__ CUtensorMap tmap, const FourierArgs a) {
   using C = FCfg<N>;
@@ -740,7 +750,26 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
       } else {
         const int jj = local / a.RB, rb = local % a.RB;
-        row_inverse<N>(a, stage, tw, c * a.B + jj, jj, rb, slot);
+        const float2 pe = row_inverse<N, PSIERR>(a, stage, tw, c * a.B + jj, jj, rb, slot);
+        if constexpr (PSIERR) {
+          // this task's exit-wave change sums, in FP64 across the CTA
+          double d2 = pe.x, n2 = pe.y;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+            n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+          }
+          __shared__ double s_pe[2][kThreads / 32];
+          if ((threadIdx.x & 31) == 0) { s_pe[0][threadIdx.x >> 5] = d2; s_pe[1][threadIdx.x >> 5] = n2; }
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            double td = 0.0, tn = 0.0;
+            for (int i = 0; i < kThreads / 32; ++i) { td += s_pe[0][i]; tn += s_pe[1][i]; }
+            double* out = a.psi_part + 2 * ((size_t)(c * a.B + jj) * a.RB + rb);
+            out[0] = td;
+            out[1] = tn;
+          }
+        }
       }
     }
     // Publish the task: the barrier orders every thread's writes before
@@ -824,16 +853,22 @@ size_t fourier_smem_bytes(int N, int M, int bufs, int G) {
 }
 
 // The single-scan kernel: the gang form for every frame size, and for
-// N = 256 also the one-strip form (the modes fill the slots by themselves).
-static const void* fourier_kernel(int N, bool gang) {
+// N = 256 also the one-strip form (the modes fill the slots by themselves);
+// each with and without the exit-wave change sums.
+template <bool PSIERR>
+static const void* fourier_kernel_t(int N, bool gang) {
   switch (N) {
-    case 16: return (const void*)k_fourier<16, true>;
-    case 32: return (const void*)k_fourier<32, true>;
-    case 64: return (const void*)k_fourier<64, true>;
-    case 128: return (const void*)k_fourier<128, true>;
-    case 256: return gang ? (const void*)k_fourier<256, true> : (const void*)k_fourier<256, false>;
+    case 16: return (const void*)k_fourier<16, true, PSIERR>;
+    case 32: return (const void*)k_fourier<32, true, PSIERR>;
+    case 64: return (const void*)k_fourier<64, true, PSIERR>;
+    case 128: return (const void*)k_fourier<128, true, PSIERR>;
+    case 256: return gang ? (const void*)k_fourier<256, true, PSIERR> : (const void*)k_fourier<256, false, PSIERR>;
     default: return nullptr;
   }
+}
+
+static const void* fourier_kernel(int N, bool gang, bool psierr) {
+  return psierr ? fourier_kernel_t<true>(N, gang) : fourier_kernel_t<false>(N, gang);
 }
 
 // The dynamic shared-memory limit is a property of the kernel, shared by
@@ -847,18 +882,19 @@ static cudaError_t allow_max_smem(const void* f) {
   return e;
 }
 
-// Resident CTAs per SM of the single-scan kernel (the smaller of its two
-// forms), with both forms' shared-memory limits set.
+// Resident CTAs per SM of the single-scan kernel (the smallest over its
+// forms), with every form's shared-memory limit set.
 int fourier_occupancy(int N, size_t smem) {
   int best = -1;
-  for (bool gang : {true, false}) {
-    const void* f = fourier_kernel(N, gang);
-    if (!f) return 0;
-    if (allow_max_smem(f) != cudaSuccess) return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, smem) != cudaSuccess) return 0;
-    best = best < 0 ? nb : (nb < best ? nb : best);
-  }
+  for (bool psierr : {false, true})
+    for (bool gang : {true, false}) {
+      const void* f = fourier_kernel(N, gang, psierr);
+      if (!f) return 0;
+      if (allow_max_smem(f) != cudaSuccess) return 0;
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, smem) != cudaSuccess) return 0;
+      best = best < 0 ? nb : (nb < best ? nb : best);
+    }
   return best;
 }
 
@@ -898,20 +934,28 @@ int fourier_batch_occupancy(int N, size_t smem) {
   return nb;
 }
 
-cudaError_t launch_fourier(const void* tmap, const FourierArgs& a, int grid, size_t smem, cudaStream_t s) {
-  const CUtensorMap& m = *static_cast<const CUtensorMap*>(tmap);
+template <bool PSIERR>
+static cudaError_t launch_fourier_t(const CUtensorMap& m, const FourierArgs& a, int grid, size_t smem,
+                                    cudaStream_t s) {
   switch (a.N) {
-    case 16: k_fourier<16, true><<<grid, kThreads, smem, s>>>(m, a); break;
-    case 32: k_fourier<32, true><<<grid, kThreads, smem, s>>>(m, a); break;
-    case 64: k_fourier<64, true><<<grid, kThreads, smem, s>>>(m, a); break;
-    case 128: k_fourier<128, true><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 16: k_fourier<16, true, PSIERR><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 32: k_fourier<32, true, PSIERR><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 64: k_fourier<64, true, PSIERR><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 128: k_fourier<128, true, PSIERR><<<grid, kThreads, smem, s>>>(m, a); break;
     case 256:
-      if (a.G > 1) k_fourier<256, true><<<grid, kThreads, smem, s>>>(m, a);
-      else k_fourier<256, false><<<grid, kThreads, smem, s>>>(m, a);
+      if (a.G > 1) k_fourier<256, true, PSIERR><<<grid, kThreads, smem, s>>>(m, a);
+      else k_fourier<256, false, PSIERR><<<grid, kThreads, smem, s>>>(m, a);
       break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+// The instance follows the plan: the gang form when G > 1, the exit-wave
+// change sums when a.psi_part is set.
+cudaError_t launch_fourier(const void* tmap, const FourierArgs& a, int grid, size_t smem, cudaStream_t s) {
+  const CUtensorMap& m = *static_cast<const CUtensorMap*>(tmap);
+  return a.psi_part ? launch_fourier_t<true>(m, a, grid, smem, s) : launch_fourier_t<false>(m, a, grid, smem, s);
 }
 
 }  // namespace dmk

@@ -19,6 +19,9 @@ enum : int {
 constexpr int kThreads = 256;          // threads per CTA of every hot kernel
 constexpr int kMetricsRing = 1024;     // iterations of metrics kept on the device
 constexpr int kMaxModes = 16;
+// One metrics row: eps_obj, fourier_err, eps_probe[kMaxModes], eps_psi.
+constexpr int kRingRow = 3 + kMaxModes;
+constexpr int kRingPsi = 2 + kMaxModes;
 constexpr int kStripW = 2;             // columns per Fourier column strip
 constexpr int kMaxStripBufs = 3;       // strip buffers of a column task
 constexpr int kTwBytes = 2048;         // shared twiddle table (N <= 256 complex values)
@@ -46,6 +49,8 @@ struct FourierArgs {
   float2* cview;          // [J][N][N] object source sum_k conj(P_k) psi_k
   float2* scratch;        // [nslot][B][M][N][N]
   double* ef_part;        // [J][CG] Fourier-error numerator partials
+  double* psi_part;       // [J][RB][2] per I task: sum |psi' - psi|^2, sum |psi'|^2 (null: not
+                          // tracked; the kernel instance must match, see launch_fourier)
   const float2* tw;       // twiddle tables (fourier_twiddles)
   int B, nchunks, lag, nslot;
   int RB;                 // row tasks per view (row blocks)
@@ -176,8 +181,8 @@ cudaError_t launch_reduce_sum(const double* in, long long n, int stride, int off
                               cudaStream_t s);
 cudaError_t launch_metrics(const double* ef_part, long long n_ef, const double* isum,
                            const double* obj_part, int n_obj, const double* probe_part,
-                           int n_probe, int M, int probe_updated, double* ring, long long* iter,
-                           int* status, cudaStream_t s);
+                           int n_probe, int M, int probe_updated, const double* psi_part, long long n_psi,
+                           double* ring, long long* iter, int* status, cudaStream_t s);
 cudaError_t launch_mode_power(const float2* probe, int N, int M, double* out, cudaStream_t s);
 
 // Batched 2-D DFT of 256 x 256 frames (dm_dft.cu): tables and limits once

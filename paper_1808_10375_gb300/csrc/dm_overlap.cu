@@ -441,13 +441,15 @@ __global__ void __launch_bounds__(kThreads) k_reduce_sum(const double* in, long 
   if (threadIdx.x == 0) *out = s;
 }
 
-// Eq. 6 for the object and each probe mode, and the Fourier error, into the
-// metrics ring (row = [eps_obj, fourier_err, eps_probe[0..M-1]]).
+// Eq. 6 for the object and each probe mode, the Fourier error and (when the
+// Fourier step tracked it, n_psi > 0) the exit-wave change into the metrics
+// ring (row = [eps_obj, fourier_err, eps_probe[0..kMaxModes-1], eps_psi]; an
+// untracked eps_psi is NaN).
 __global__ void __launch_bounds__(kThreads) k_metrics(const double* ef_part, long long n_ef, const double* isum,
                                                       const double* obj_part, int n_obj,
                                                       const double* probe_part, int n_probe, int M,
-                                                      int probe_updated, double* ring, long long* iter,
-                                                      int* status) {
+                                                      int probe_updated, const double* psi_part, long long n_psi,
+                                                      double* ring, long long* iter, int* status) {
   __shared__ double sh[kThreads / 32];
   __shared__ int s_slot;
   // the ring slot comes from the device-side iteration counter, so that a
@@ -462,7 +464,14 @@ __global__ void __launch_bounds__(kThreads) k_metrics(const double* ef_part, lon
   for (int i = threadIdx.x; i < n_obj; i += kThreads) { od += obj_part[2 * i]; on += obj_part[2 * i + 1]; }
   od = block_sum(od, sh);
   on = block_sum(on, sh);
-  double* row = ring + (size_t)slot * (2 + kMaxModes);
+  double* row = ring + (size_t)slot * kRingRow;
+  {
+    double pd = 0.0, pn = 0.0;
+    for (long long i = threadIdx.x; i < n_psi; i += kThreads) { pd += psi_part[2 * i]; pn += psi_part[2 * i + 1]; }
+    pd = block_sum(pd, sh);
+    pn = block_sum(pn, sh);
+    if (threadIdx.x == 0) row[kRingPsi] = n_psi <= 0 ? nan("") : (pn > 0.0 ? sqrt(pd / pn) : 0.0);
+  }
   bool bad = false;
   if (threadIdx.x == 0) {
     const double is = *isum;
@@ -626,9 +635,10 @@ cudaError_t launch_reduce_sum(const double* in, long long n, int stride, int off
 
 cudaError_t launch_metrics(const double* ef_part, long long n_ef, const double* isum, const double* obj_part,
                            int n_obj, const double* probe_part, int n_probe, int M, int probe_updated,
-                           double* ring, long long* iter, int* status, cudaStream_t s) {
+                           const double* psi_part, long long n_psi, double* ring, long long* iter, int* status,
+                           cudaStream_t s) {
   k_metrics<<<1, kThreads, 0, s>>>(ef_part, n_ef, isum, obj_part, n_obj, probe_part, n_probe, M, probe_updated,
-                                   ring, iter, status);
+                                   psi_part, n_psi, ring, iter, status);
   return cudaGetLastError();
 }
 

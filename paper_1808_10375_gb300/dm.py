@@ -52,7 +52,7 @@ class DMError(RuntimeError):
 
 EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_object", "dm_get_probe",
            "dm_get_exit_waves", "dm_set_exit_waves", "dm_set_object", "dm_set_probe", "dm_get_error",
-           "dm_iterations_done", "dm_get_mode_power", "dm_sync", "dm_set_timing", "dm_get_timing",
+           "dm_set_psi_error", "dm_get_psi_error", "dm_iterations_done", "dm_get_mode_power", "dm_sync", "dm_set_timing", "dm_get_timing",
            "dm_kernel_name", "dm_device_bytes", "dm_free", "dm_last_error", "dm_probe_update_static",
            "dm_object_partials", "dm_object_apply", "dm_probe_partials", "dm_probe_apply",
            "dm_fourier_error_partials", "dm_finish_iteration", "dm_set_graph", "dm_autotune",
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
         "dm_set_object": (ctypes.c_int, [vp, vp, i32]),
         "dm_set_probe": (ctypes.c_int, [vp, vp, i32]),
         "dm_get_error": (ctypes.c_int, [vp, i32, dp, dp, dp]),
+        "dm_set_psi_error": (ctypes.c_int, [vp, i32]),
+        "dm_get_psi_error": (ctypes.c_int, [vp, i32, dp]),
         "dm_iterations_done": (i64, [vp]),
         "dm_get_mode_power": (ctypes.c_int, [vp, dp]),
         "dm_sync": (ctypes.c_int, [vp]),
@@ -558,6 +560,19 @@ def dm_get_error(ctx: Context, iteration: int = -1):
     ep = (ctypes.c_double * ctx.params.modes)()
     _check(load().dm_get_error(ctx.handle, int(iteration), ctypes.byref(eo), ep, ctypes.byref(ef)), ctx)
     return eo.value, list(ep), ef.value
+
+
+def dm_set_psi_error(ctx: Context, enable: bool = True):
+    """Track the exit-wave change eps_psi in the following iterations (the
+    Fourier step then reads the old exit waves back)."""
+    _check(load().dm_set_psi_error(ctx.handle, 1 if enable else 0), ctx)
+
+
+def dm_get_psi_error(ctx: Context, iteration: int = -1) -> float:
+    """eps_psi of one iteration (NaN where it was not tracked)."""
+    out = ctypes.c_double()
+    _check(load().dm_get_psi_error(ctx.handle, int(iteration), ctypes.byref(out)), ctx)
+    return out.value
 
 
 def dm_iterations_done(ctx: Context) -> int:
