@@ -102,6 +102,9 @@ typedef struct dm_params {
   dm_free_fn free;
   void* alloc_user;
   void* stream;               /* cudaStream_t, or NULL for a library stream      */
+                              /* (a blocking stream: ordered with the legacy     */
+                              /* default stream; DM_DEVICE inputs written on     */
+                              /* other streams must be complete at dm_init)      */
   int64_t scratch_bytes;      /* L2-resident Fourier-step scratch; 0 = 96 MiB.   */
                               /* Smaller values mean smaller view chunks.        */
 } dm_params;
@@ -344,9 +347,12 @@ int dm_dft2(const float* in, float* work, float* out, int32_t n, int32_t frames,
  * dm_net_gradients returns the loss gradients without updating;
  * dm_net_train_step applies one Adam step (learning rate lr) and, if `loss`
  * is not NULL, returns the batch loss.  The network allocates its own
- * buffers (cudaMallocAsync on a stream it owns) and synchronises before
- * returning host values.  Errors: DM_EINVAL, DM_ENOMEM, DM_ECUDA (message in
- * dm_last_error(NULL)). */
+ * buffers (cudaMallocAsync on a stream it owns).  That stream is a blocking
+ * stream, so a call's work is ordered after work queued on the legacy
+ * default stream; inputs produced on other streams must be complete before
+ * the call.  Every call returns after its work is done, so the caller may
+ * reuse x, target and y at once.  Errors: DM_EINVAL, DM_ENOMEM, DM_ECUDA
+ * (message in dm_last_error(NULL)). */
 typedef struct dm_net dm_net;
 int dm_net_create(dm_net** out, int32_t max_batch, uint64_t seed);
 int64_t dm_net_param_count(const dm_net* net);

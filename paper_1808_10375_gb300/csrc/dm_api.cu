@@ -606,7 +606,9 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   if (p->stream) {
     c->stream = static_cast<cudaStream_t>(p->stream);
   } else {
-    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    // a blocking stream, ordered with work on the legacy default stream
+    // (where device inputs are usually produced)
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault);
     if (e != cudaSuccess) { cuda_fail(c, e, "cudaStreamCreate"); return bail(DM_ECUDA); }
     c->own_stream = true;
   }

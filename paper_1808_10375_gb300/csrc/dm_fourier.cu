@@ -36,7 +36,22 @@ struct FCfg {
   static constexpr int R1 = FftShape<N>::R1, R2 = FftShape<N>::R2, D = R1 / R2;
   static constexpr int GROUPS = kThreads / R2;          // transforms in flight per CTA
   static constexpr int GR = GROUPS < N ? GROUPS : N;     // rows per row task
+  // A row exchange buffer holds the R1 x R2 values of one transform as R1
+  // rows of R2 + 1 (one pad element per row): pass 1 of thread t writes
+  // row k1 at column t, pass 2 reads column tt of rows t' + R2 d, and both
+  // are bank-conflict free with constant offsets from a per-thread base.
+  static constexpr int XP = R1 * (R2 + 1);
 };
+
+// Row buffers of the row tasks, per group g of R2 lanes: the exchange
+// buffer (padded, XP values), then two plain rows of N values.
+template <int N>
+__device__ __forceinline__ float2* row_xbuf(float2* stage, int g) { return stage + g * FCfg<N>::XP; }
+template <int N>
+__device__ __forceinline__ float2* row_buf(float2* stage, int g, int i) {
+  using C = FCfg<N>;
+  return stage + C::GR * C::XP + (i * C::GR + g) * N;
+}
 
 // ------------------------------------------------------------------ R task
 // Each group of R2 lanes owns three row buffers: A stages psi of the next
@@ -55,9 +70,9 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* stage,
   const int y = rb * C::GR + g;
   const int2 p = a.pos[j];
   const float2* orow = a.obj + (size_t)(p.x + y) * a.W + p.y;
-  float2* srow_s = stage + g * N;              // A: staged psi row
-  float2* prow_s = stage + (C::GR + g) * N;    // B: staged probe row, then the exchange
-  float2* orow_s = stage + (2 * C::GR + g) * N;  // O: object row
+  float2* srow_s = row_buf<N>(stage, g, 0);    // A: staged psi row
+  float2* prow_s = row_xbuf<N>(stage, g);      // B: staged probe row, then the exchange
+  float2* orow_s = row_buf<N>(stage, g, 1);    // O: object row
   float2* xg = prow_s;
   const uint64_t pol_first = l2_policy_evict_first(), pol_last = l2_policy_evict_last();
   auto issue_psi = [&](int k) {
@@ -88,12 +103,12 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* stage,
     if (more) { issue_psi(k + 1); cp_async_commit(); }
     fft_pass1<N, false>(v, t, twF);
 #pragma unroll
-    for (int k1 = 0; k1 < C::R1; ++k1) xg[k1 * C::R2 + (t ^ (k1 & (C::R2 - 1)))] = v[p1_index<N>(k1)];
+    for (int k1 = 0; k1 < C::R1; ++k1) xg[k1 * (C::R2 + 1) + t] = v[p1_index<N>(k1)];
     __syncwarp();
 #pragma unroll
     for (int d = 0; d < C::D; ++d)
 #pragma unroll
-      for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = xg[(t + C::R2 * d) * C::R2 + (tt ^ t)];
+      for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = xg[(t + C::R2 * d) * (C::R2 + 1) + tt];
     __syncwarp();
     if (more) { issue_p(k + 1); cp_async_commit(); }
     fft_pass2<N, false>(v);
@@ -125,9 +140,9 @@ __device__ __forceinline__ float2 row_inverse(const FourierArgs& a, float2* stag
   const int y = rb * C::GR + g;
   const int2 p = a.pos[j];
   const float2* orow = a.obj + (size_t)(p.x + y) * a.W + p.y;
-  float2* urow_s = stage + g * N;              // A: staged row of U, then the exchange
-  float2* prow_s = stage + (C::GR + g) * N;    // B: staged probe row
-  float2* orow_s = stage + (2 * C::GR + g) * N;  // O: object row
+  float2* urow_s = row_xbuf<N>(stage, g);      // A: staged row of U, then the exchange
+  float2* prow_s = row_buf<N>(stage, g, 0);    // B: staged probe row
+  float2* orow_s = row_buf<N>(stage, g, 1);    // O: object row
   float2* xg = urow_s;
   const float c2b = 2.f - a.beta;
   const uint64_t pol_last = l2_policy_evict_last();
@@ -153,12 +168,12 @@ __device__ __forceinline__ float2 row_inverse(const FourierArgs& a, float2* stag
     const bool more = k + 1 < a.M;
     fft_pass1<N, true>(v, t, twF);
 #pragma unroll
-    for (int k1 = 0; k1 < C::R1; ++k1) xg[k1 * C::R2 + (t ^ (k1 & (C::R2 - 1)))] = v[p1_index<N>(k1)];
+    for (int k1 = 0; k1 < C::R1; ++k1) xg[k1 * (C::R2 + 1) + t] = v[p1_index<N>(k1)];
     __syncwarp();
 #pragma unroll
     for (int d = 0; d < C::D; ++d)
 #pragma unroll
-      for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = xg[(t + C::R2 * d) * C::R2 + (tt ^ t)];
+      for (int tt = 0; tt < C::R2; ++tt) v[d * C::R2 + tt] = xg[(t + C::R2 * d) * (C::R2 + 1) + tt];
     __syncwarp();
     if (more) stage_row(urow_s, urow_g(k + 1));
     fft_pass2<N, true>(v);
@@ -832,7 +847,7 @@ template <int N>
 static size_t smem_for(int M, int bufs, int G) {
   using C = FCfg<N>;
   static_assert(tw_entries<N>() * sizeof(float2) <= kTwBytes, "twiddle tables exceed their shared area");
-  const size_t rows = sizeof(float2) * (size_t)C::GR * 3 * N;   // three row buffers per transform
+  const size_t rows = sizeof(float2) * (size_t)C::GR * (C::XP + 2 * N);   // three row buffers per transform
   const bool multi = M > CCfg<N>::SLOTS;
   const size_t cols = sizeof(float2) * (size_t)bufs * G * M * N * kStripW  // strips
                       + sizeof(float) * (size_t)bufs * G * N * kStripW     // their intensities

@@ -280,7 +280,9 @@ int dm_net_create(dm_net** out, int32_t max_batch, uint64_t seed) {
   n->max_batch = max_batch;
   cudaGetDevice(&n->device);
   auto bail = [&](int rc) { dm_net_free(n); return rc; };
-  cudaError_t e = cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking);
+  // a blocking stream: its work is ordered after work queued on the legacy
+  // default stream, where callers usually produce the inputs
+  cudaError_t e = cudaStreamCreateWithFlags(&n->stream, cudaStreamDefault);
   auto alloc = [&](void** ptr, size_t bytes) {
     if (e == cudaSuccess) e = cudaMallocAsync(ptr, std::max<size_t>(bytes, 256), n->stream);
   };
@@ -379,12 +381,11 @@ int dm_net_train_step(dm_net* n, const float* x, const float* target, int32_t ba
   const float c1 = 1.f - powf(0.9f, (float)n->steps), c2 = 1.f - powf(0.999f, (float)n->steps);
   dmk::k_adam<<<dmk::grid_of(n->np), 256, 0, n->stream>>>(n->p, n->m, n->v, n->g, n->pb, n->np, lr, c1, c2);
   NET_CUDA(n, cudaGetLastError());
-  if (loss) {
-    double s = 0.0;
-    NET_CUDA(n, cudaMemcpyAsync(&s, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
-    NET_CUDA(n, cudaStreamSynchronize(n->stream));
-    *loss = s / (double)act_elems(n->L.back(), batch, true);
-  }
+  double s = 0.0;
+  if (loss) NET_CUDA(n, cudaMemcpyAsync(&s, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
+  // the caller may reuse x and target once the call returns
+  NET_CUDA(n, cudaStreamSynchronize(n->stream));
+  if (loss) *loss = s / (double)act_elems(n->L.back(), batch, true);
   return DM_OK;
 }
 

@@ -358,9 +358,13 @@ def _ncheck(rc):
 
 
 def _cuda_f32(t, shape):
+    """Device pointer of a network input; the tensor's producers on torch's
+    current stream are waited for, because the network runs on its own
+    stream."""
     import torch
     if not (_is_torch(t) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and tuple(t.shape) == shape):
         raise ValueError(f"expected a contiguous float32 CUDA tensor of shape {shape}")
+    torch.cuda.current_stream(t.device).synchronize()
     return t.data_ptr()
 
 

@@ -49,11 +49,13 @@ def test_forward_and_gradients_match_the_reference():
 
 def test_warm_start_is_trained_and_judged_by_dm():
     """The network trains on simulated pairs with the library's kernels, its
-    stitched start is judged by DM's own Fourier error, and the judged start
-    is never worse than the flat start by more than the trial can tell.  On
-    these random-field objects the network gains nothing (its start error
-    and DM's convergence match the flat start's); the test records the
-    comparison and checks the fallback."""
+    stitched start is judged by DM's own Fourier error (the start with the
+    lower error after the trial iterations is kept), and DM converges from
+    both starts.  On these random-field objects the network gains nothing:
+    its start error is the flat start's, and the trial's Fourier errors
+    differ by a few per cent, so the judge's pick does not predict which
+    start ends lower after 60 iterations.  The test records the comparison
+    and checks the mechanism, not a gain."""
     from paper_1808_10375_gb300 import dm, warmstart
     from synth import make_scan
     from synth import warmstart as ws
@@ -71,6 +73,25 @@ def test_warm_start_is_trained_and_judged_by_dm():
         e = dict(res[name]["errors"])
         print(name, "start error", round(e[0], 4), "after 20 / 60 iterations", round(e[20], 4), round(e[60], 4))
     print("judge:", pick, ef)
-    final = {name: dict(res[name]["errors"])[60] for name in ("flat", "warm")}
-    assert final[pick] <= 1.05 * final["flat"]
+    assert pick == min(ef, key=ef.get)
+    assert np.array_equal(o0, o_warm.detach().cpu().numpy().astype(np.complex64) if pick == "warm"
+                          else np.ones(scan.obj_shape, np.complex64))
+    for name in ("flat", "warm"):
+        e = dict(res[name]["errors"])
+        assert e[60] <= 0.25 * e[0], (name, e[0], e[60])
     dm.dm_net_free(net)
+
+
+def test_training_is_reproducible():
+    """Two networks from the same seed, trained on the same seeded batches
+    (gathered by torch right before each call, as warmstart.train does), end
+    with bit-identical parameters: every network kernel is deterministic, and
+    each call waits for its inputs and finishes before returning."""
+    from paper_1808_10375_gb300 import dm, warmstart
+    params = []
+    for _ in range(2):
+        net = dm.dm_net_create(max_batch=32, seed=3)
+        warmstart.train(net, steps=40, batch=32, lr=1e-3, seed=4, data_count=512)
+        params.append(dm.dm_net_get_params(net))
+        dm.dm_net_free(net)
+    assert np.array_equal(params[0], params[1])
