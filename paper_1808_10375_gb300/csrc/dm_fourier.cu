@@ -360,9 +360,14 @@ __device__ __forceinline__ float col_factor(const float* nrm, int nstride, const
 #pragma unroll
     for (int k = 0; k < MM; ++k)
       if (k < M) S += ng[k * nstride];
-    const float si_ = sqrtf(ib[p]);
-    const float ss = sqrtf(S);
-    const float sc = (S > 0.f) ? (si_ / ss) * invN : 0.f;
+    // sqrt(I), sqrt(S) and sqrt(I)/sqrt(S) from two reciprocal square roots
+    // (rsqrtf, a few ulp): the factor needs FP32 relative accuracy, not
+    // correct rounding, and this step sits between two block barriers
+    const float iv = ib[p];
+    const float ri = rsqrtf(iv), rs = rsqrtf(S);
+    const float si_ = iv > 0.f ? iv * ri : 0.f;
+    const float ss = S > 0.f ? S * rs : 0.f;
+    const float sc = S > 0.f ? si_ * rs * invN : 0.f;
     const float dd = fmaf(ss, invN, -si_);
     ef = fmaf(dd, dd, ef);
     fb[p] = fmaf(beta, sc, -invN2);
