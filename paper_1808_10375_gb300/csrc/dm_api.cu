@@ -426,8 +426,8 @@ int plan_probe(dm_ctx* c) {
   const int nn = c->N * c->N;
   const int tp = dmk::probe_tile_px(c->M);
   const int tiles = (nn + tp - 1) / tp;
-  // view groups such that tiles x groups work items split evenly over one
-  // persistent CTA per SM
+  // view groups such that tiles x groups work items are a multiple of the SM
+  // count (the probe-partial grid has two persistent CTAs per SM)
   int g = c->num_sms / std::gcd(tiles, c->num_sms);
   g = std::max(1, std::min(g, c->J));
   c->probe_groups = g;

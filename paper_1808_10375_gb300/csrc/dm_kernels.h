@@ -117,7 +117,7 @@ struct ObjFinalArgs {
 // FP64 reduction over the groups and the division.
 // ---------------------------------------------------------------------------
 constexpr int kProbePxPerThread = 2;   // pixels per thread for M <= 8 (1 above)
-constexpr int kProbeStages = 4;        // depth of the views' shared-memory ring
+constexpr int kProbeStages = 3;        // depth of the views' shared-memory ring (2 CTAs per SM)
 
 struct ProbePartialArgs {
   int N, M, J, H, W, groups;
@@ -159,7 +159,7 @@ cudaError_t launch_obj_source(float2* cview, const float2* psi, const float2* pr
 // Pixels per probe tile and the probe-partial kernel's dynamic shared memory.
 int probe_tile_px(int M);
 size_t probe_partial_smem_bytes(int M);
-// Probe partial sums; a persistent grid of min(items, num_sms) CTAs.
+// Probe partial sums; a persistent grid of min(items, 2 num_sms) CTAs (two per SM).
 cudaError_t launch_probe_partial(const ProbePartialArgs& a, int num_sms, cudaStream_t s);
 cudaError_t prepare_probe_partial(int M);
 cudaError_t launch_probe_final(const ProbeFinalArgs& a, cudaStream_t s, int* blocks_out);

@@ -188,14 +188,14 @@ __global__ void __launch_bounds__(kThreads) k_obj_source(float2* cview, const fl
 // tile and sums over the group's views
 //   num_k(u) += conj(O(r_j + u)) psi_j^k(u),   den(u) += |O(r_j + u)|^2
 // (num in FP32, den in FP32 over 32 views then FP64), then writes the item's
-// partials.  A persistent CTA per SM streams the views through a
+// partials.  Persistent CTAs (two per SM) stream the views through a
 // kProbeStages-deep shared-memory ring: one bulk asynchronous copy per mode
 // brings the tile of psi_j^k (contiguous in memory), and each thread copies
 // the object values of its own pixels with 8-byte asynchronous copies, so
 // several views' reads are in flight while one is summed.
 // ---------------------------------------------------------------------------
 template <int MAXM, int PX>
-__global__ void __launch_bounds__(kThreads, 1) k_probe_partial(const ProbePartialArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_probe_partial(const ProbePartialArgs a) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kProbeStages];
   constexpr int TP = PX * kThreads;  // pixels per tile
@@ -534,7 +534,8 @@ static cudaError_t probe_partial_launch(const ProbePartialArgs& a, int num_sms, 
   if (e != cudaSuccess) return e;
   const int tp = PX * kThreads;
   const int items = ((a.N * a.N + tp - 1) / tp) * a.groups;
-  k_probe_partial<MAXM, PX><<<std::min(items, num_sms), kThreads, smem, s>>>(a);
+  // two CTAs per SM: one CTA's per-view barrier overlaps the other's sums
+  k_probe_partial<MAXM, PX><<<std::min(items, 2 * num_sms), kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
