@@ -377,15 +377,26 @@ __global__ void __launch_bounds__(kThreads) k_probe_div(const ProbeFinalArgs a) 
 // psi_j^k(u) = P_k(u) O(r_j + u): the initial fields (Sec. II, first step).
 __global__ void __launch_bounds__(kThreads) k_init_psi(float2* psi, const float2* probe, const float2* obj,
                                                        const int2* pos, int N, int M, int J, int W) {
-  const size_t nn = (size_t)N * N;
-  const size_t tot = (size_t)J * M * nn;
-  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < tot; i += (size_t)gridDim.x * kThreads) {
-    const size_t u = i % nn;
-    const size_t jk = i / nn;
+  // one warp per (view, mode, row); each lane forms two adjacent values and
+  // writes them with one 16-byte streaming store (N is even, rows 16-byte
+  // aligned); the index arithmetic is done once per row
+  const long long nrows = (long long)J * M * N;
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * (kThreads / 32);
+  for (long long r = (long long)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); r < nrows; r += nwarps) {
+    const int y = (int)(r % N);
+    const long long jk = r / N;
     const int k = (int)(jk % M), j = (int)(jk / M);
-    const int y = (int)(u / N), x = (int)(u % N);
     const int2 p = pos[j];
-    psi[i] = cmul(probe[k * nn + u], obj[(size_t)(p.x + y) * W + p.y + x]);
+    const float2* prow = probe + ((size_t)k * N + y) * N;
+    const float2* orow = obj + (size_t)(p.x + y) * W + p.y;
+    float2* dst = psi + (size_t)r * N;
+    for (int x = 2 * lane; x < N; x += 64) {
+      const float4 pv = *reinterpret_cast<const float4*>(prow + x);
+      const float2 a = cmul(make_float2(pv.x, pv.y), orow[x]);
+      const float2 b = cmul(make_float2(pv.z, pv.w), orow[x + 1]);
+      __stcs(reinterpret_cast<float4*>(dst + x), make_float4(a.x, a.y, b.x, b.y));
+    }
   }
 }
 
@@ -612,7 +623,9 @@ cudaError_t launch_max_f64(const double* x, size_t n, unsigned long long* bits, 
 
 cudaError_t launch_init_psi(float2* psi, const float2* probe, const float2* obj, const int2* pos, int N, int M,
                             int J, int W, cudaStream_t s) {
-  k_init_psi<<<grid_for((size_t)J * M * N * N, 8192), kThreads, 0, s>>>(psi, probe, obj, pos, N, M, J, W);
+  const long long rows = (long long)J * M * N;
+  const int blocks = (int)std::min<long long>((rows + kThreads / 32 - 1) / (kThreads / 32), 8192);
+  k_init_psi<<<blocks, kThreads, 0, s>>>(psi, probe, obj, pos, N, M, J, W);
   return cudaGetLastError();
 }
 
