@@ -95,7 +95,7 @@ struct dm_ctx {
   size_t counters_bytes = 0;
   int tiles_x = 0, tiles_y = 0, obj_final_blocks = 0;
   CUtensorMap tmap_c;
-  CUtensorMap tmap_s;
+  CUtensorMap tmap_s[2];   // scratch ring: box of all modes, box of one mode
   int probe_groups = 0;
   int probe_final_blocks = 0;
   int64_t iters = 0;
@@ -320,9 +320,10 @@ int fourier_schedule(dm_ctx* c, int J, const FourierKnobs& k, dmk::FourierArgs& 
   return DM_OK;
 }
 
-// TMA view of a scratch ring for the column tasks: planes of N x N complex
-// values (8-byte elements), one plane per (view, mode); a box is kStripW
-// columns x N rows x M modes.
+// TMA views of a scratch ring for the column tasks: planes of N x N complex
+// values (8-byte elements), one plane per (view, mode).  map[0]'s box is
+// kStripW columns x N rows x M modes (strip loads), map[1]'s the same with
+// one mode (the per-mode stores of U).
 int encode_scratch_map(dm_ctx* c, const dmk::FourierArgs& a, float2* scratch, CUtensorMap* map) {
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
@@ -333,13 +334,15 @@ int encode_scratch_map(dm_ctx* c, const dmk::FourierArgs& a, float2* scratch, CU
   const cuuint64_t e = sizeof(float2);
   const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)a.nslot * a.B * M};
   const cuuint64_t strides[2] = {(cuuint64_t)N * e, (cuuint64_t)N * N * e};
-  const cuuint32_t box[3] = {(cuuint32_t)a.w, (cuuint32_t)N, (cuuint32_t)M};
   const cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, scratch, dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS)
-    return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled (scratch) failed (" + std::to_string((int)r) + ")");
+  for (int i = 0; i < 2; ++i) {
+    const cuuint32_t box[3] = {(cuuint32_t)a.w, (cuuint32_t)N, (cuuint32_t)(i == 0 ? M : 1)};
+    const CUresult r = encode(map + i, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, scratch, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled (scratch) failed (" + std::to_string((int)r) + ")");
+  }
   return DM_OK;
 }
 
@@ -360,7 +363,7 @@ int plan_fourier(dm_ctx* c, const FourierKnobs& k) {
   DM_CUDA(c, cudaMemcpyAsync(c->stage_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice,
                              c->stream));
   DM_CUDA(c, cudaStreamSynchronize(c->stream));  // `off` is a host temporary
-  if ((rc = encode_scratch_map(c, a, c->scratch, &c->tmap_s))) return rc;
+  if ((rc = encode_scratch_map(c, a, c->scratch, c->tmap_s))) return rc;
   a.psi = c->psi; a.istrip = c->istrip; a.pos = c->pos; a.cview = c->cview;
   a.scratch = c->scratch; a.ef_part = c->ef_part; a.tw = c->tw;
   a.stage_off = c->stage_off; a.counters = c->counters; a.status = c->status;
@@ -447,7 +450,7 @@ int run_fourier(dm_ctx* c) {
   c->fa.probe = c->probe[c->cur_P];
   c->fa.obj = c->obj[c->cur_O];
   Timed t(c, DM_KERNEL_FOURIER);
-  DM_CUDA(c, dmk::launch_fourier(&c->tmap_s, c->fa, c->fgrid, c->fsmem, c->stream));
+  DM_CUDA(c, dmk::launch_fourier(c->tmap_s, c->fa, c->fgrid, c->fsmem, c->stream));
   return DM_OK;
 }
 
@@ -831,8 +834,8 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
     a.psi = c->psi; a.istrip = c->istrip; a.pos = c->pos; a.cview = c->cview; a.scratch = scr; a.ef_part = ef;
     a.tw = c->tw; a.stage_off = offd; a.counters = cnt; a.status = c->status;
     a.probe = c->probe[c->cur_P]; a.obj = c->obj[c->cur_O];
-    CUtensorMap map;
-    if ((rc = encode_scratch_map(c, a, scr, &map))) { release(); return rc; }
+    CUtensorMap map[2];
+    if ((rc = encode_scratch_map(c, a, scr, map))) { release(); return rc; }
     cudaError_t e = cudaMemcpyAsync(offd, pl.off.data(), pl.off.size() * sizeof(int), cudaMemcpyHostToDevice,
                                     c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -840,7 +843,7 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
     for (int r = 0; r <= kReps && e == cudaSuccess; ++r) {   // the first run warms up
       if (r == 1) e = cudaEventRecord(e0, c->stream);
       if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 3 * (size_t)a.nchunks), c->stream);
-      if (e == cudaSuccess) e = dmk::launch_fourier(&map, a, pl.grid, pl.smem, c->stream);
+      if (e == cudaSuccess) e = dmk::launch_fourier(map, a, pl.grid, pl.smem, c->stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -933,7 +936,7 @@ int enqueue_batch_iteration(dm_batch* b) {
       c->fa.probe = c->probe[c->cur_P];
       c->fa.obj = c->obj[c->cur_O];
       fb.a[s] = c->fa;
-      fb.map[s] = c->tmap_s;
+      fb.map[s] = c->tmap_s[0];
       fb.base[s] = base;
       base += c->fa.total_tasks;
       DM_BCUDA(b, cudaMemsetAsync(c->counters, 0, c->counters_bytes, b->stream));

@@ -385,8 +385,16 @@ __device__ __forceinline__ float col_factor_any(const float* nrm, int nstride, c
   return col_factor<N, kMaxModes, GANG>(nrm, nstride, ib, fb, M, G, beta, ef);
 }
 
+// With tmap1 (a box of one mode) and the modes in one round over several
+// strip buffers, each slot stores its own mode of U as soon as its inverse is
+// done, so no block barrier waits for the slowest mode before the store; a
+// slot's leader makes sure its stores have left shared memory before the
+// next barrier A (after which the buffer may be refilled), and that they have
+// completed before the task ends.  Otherwise thread 0 stores the whole strip
+// after barrier C.
 template <int N, bool GANG>
-__device__ __forceinline__ double column_task(const FourierArgs& a, const CUtensorMap* tmap, float2* sbuf,
+__device__ __forceinline__ double column_task(const FourierArgs& a, const CUtensorMap* tmap,
+                                              const CUtensorMap* tmap1, float2* sbuf,
                                               float* ibuf, float* fbuf, float* nbuf, const float2* twF,
                                               uint64_t* bars, Pipe& pp, int j, int zview, int sg) {
   using C = CCfg<N>;
@@ -406,6 +414,8 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
   const unsigned mask = slot_mask<N>();
   const int rounds = (M + C::SLOTS - 1) / C::SLOTS;
   const int nsi = a.SPG / G;                  // gangs of strips in this task
+  const bool slot_store = tmap1 != nullptr && rounds == 1 && nbufs > 1;
+  const bool leader = (tid & (C::TPM - 1)) == 0 && slot < G * M;   // one lane per busy slot
   // norms: in a single round each slot's part of the strip is free once its
   // forward transform is done; otherwise in the separate buffer
   const int nstride = rounds == 1 ? 2 * N * SW : N * SW;   // floats per mode
@@ -464,6 +474,7 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
     // intensities of strips after si may still be in flight (one group per strip)
     const int later = issued - si - 1;
     if (later >= 2) cp_async_wait<2>(); else if (later == 1) cp_async_wait<1>(); else cp_async_wait<0>();
+    if (slot_store && leader) bulk_wait_read<0>();   // this slot's earlier stores have left the buffers
     __syncthreads();   // A: every mode's norms (and this strip's intensities) are in place
     if (issued < nsi && issued - si < nbufs) {
       // strip `issued` goes to the buffer of strip issued - nbufs <= si - 1,
@@ -491,6 +502,19 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
         }
       }
     }
+    if (slot_store) {
+      // each slot's U goes back on its own once the slot's lanes have written it
+      if (slot < G * M) {
+        fence_proxy_async_smem();
+        __syncwarp(mask);
+        if (leader) {
+          const int g = GANG ? slot / M : 0, k = GANG ? slot - g * M : slot;
+          tma_store_3d_hint(tmap1, (s + g) * SW, 0, zview + k, sb + (size_t)slot * N * SW, pol_last);
+          bulk_commit();
+        }
+      }
+      continue;
+    }
     fence_proxy_async_smem();
     __syncthreads();   // C: U of every mode is in the strip
     if (tid == 0) {
@@ -504,6 +528,7 @@ __device__ __forceinline__ double column_task(const FourierArgs& a, const CUtens
       ++issued;
     }
   }
+  if (slot_store && leader) bulk_wait<0>();   // the slot's stores are complete before the task is published
   return (double)ef;
 }
 
@@ -618,8 +643,8 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
         float* ibuf = reinterpret_cast<float*>(work + (size_t)a.strip_bufs * G * a.M * N * kStripW);
         float* fbuf = ibuf + (size_t)a.strip_bufs * G * N * kStripW;   // modulus factors of the current gang
         float* nbuf = fbuf + N * kStripW;                              // norms when the modes take several rounds
-        double ef = column_task<N, true>(a, maps + sc, sbuf, ibuf, fbuf, nbuf, tw, bars, pp, j, (sl * a.B + jj) * a.M,
-                                   sg);
+        double ef = column_task<N, true>(a, maps + sc, nullptr, sbuf, ibuf, fbuf, nbuf, tw, bars, pp, j,
+                                         (sl * a.B + jj) * a.M, sg);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ef += __shfl_xor_sync(0xffffffffu, ef, o);
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = ef;
@@ -657,7 +682,8 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
 // allocation lean); its task counter is counters[0].
 template <int N, bool GANG, bool PSIERR>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_fourier(const __grid_constant__ CUtensorMap tmap, const FourierArgs a) {
+    k_fourier(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap1,
+              const FourierArgs a) {
   using C = FCfg<N>;
   extern __shared__ unsigned char smem_raw[];
   // 128-byte aligned base (TMA boxes land at 128-byte aligned addresses)
@@ -758,7 +784,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       } else if (kind == 1) {
         const int jj = local / a.CG, sg = local % a.CG;
         const int j = c * a.B + jj;
-        double ef = column_task<N, GANG>(a, &tmap, sbuf, ibuf, fbuf, nbuf, tw, bars, pp, j, (sl * a.B + jj) * a.M, sg);
+        double ef = column_task<N, GANG>(a, &tmap, &tmap1, sbuf, ibuf, fbuf, nbuf, tw, bars, pp, j,
+                                         (sl * a.B + jj) * a.M, sg);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ef += __shfl_xor_sync(0xffffffffu, ef, o);
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = ef;
@@ -955,16 +982,16 @@ int fourier_batch_occupancy(int N, size_t smem) {
 }
 
 template <bool PSIERR>
-static cudaError_t launch_fourier_t(const CUtensorMap& m, const FourierArgs& a, int grid, size_t smem,
-                                    cudaStream_t s) {
+static cudaError_t launch_fourier_t(const CUtensorMap& m, const CUtensorMap& m1, const FourierArgs& a, int grid,
+                                    size_t smem, cudaStream_t s) {
   switch (a.N) {
-    case 16: k_fourier<16, true, PSIERR><<<grid, kThreads, smem, s>>>(m, a); break;
-    case 32: k_fourier<32, true, PSIERR><<<grid, kThreads, smem, s>>>(m, a); break;
-    case 64: k_fourier<64, true, PSIERR><<<grid, kThreads, smem, s>>>(m, a); break;
-    case 128: k_fourier<128, true, PSIERR><<<grid, kThreads, smem, s>>>(m, a); break;
+    case 16: k_fourier<16, true, PSIERR><<<grid, kThreads, smem, s>>>(m, m1, a); break;
+    case 32: k_fourier<32, true, PSIERR><<<grid, kThreads, smem, s>>>(m, m1, a); break;
+    case 64: k_fourier<64, true, PSIERR><<<grid, kThreads, smem, s>>>(m, m1, a); break;
+    case 128: k_fourier<128, true, PSIERR><<<grid, kThreads, smem, s>>>(m, m1, a); break;
     case 256:
-      if (a.G > 1) k_fourier<256, true, PSIERR><<<grid, kThreads, smem, s>>>(m, a);
-      else k_fourier<256, false, PSIERR><<<grid, kThreads, smem, s>>>(m, a);
+      if (a.G > 1) k_fourier<256, true, PSIERR><<<grid, kThreads, smem, s>>>(m, m1, a);
+      else k_fourier<256, false, PSIERR><<<grid, kThreads, smem, s>>>(m, m1, a);
       break;
     default: return cudaErrorInvalidValue;
   }
@@ -973,9 +1000,10 @@ static cudaError_t launch_fourier_t(const CUtensorMap& m, const FourierArgs& a, 
 
 // The instance follows the plan: the gang form when G > 1, the exit-wave
 // change sums when a.psi_part is set.
-cudaError_t launch_fourier(const void* tmap, const FourierArgs& a, int grid, size_t smem, cudaStream_t s) {
-  const CUtensorMap& m = *static_cast<const CUtensorMap*>(tmap);
-  return a.psi_part ? launch_fourier_t<true>(m, a, grid, smem, s) : launch_fourier_t<false>(m, a, grid, smem, s);
+cudaError_t launch_fourier(const void* tmaps, const FourierArgs& a, int grid, size_t smem, cudaStream_t s) {
+  const CUtensorMap* m = static_cast<const CUtensorMap*>(tmaps);
+  return a.psi_part ? launch_fourier_t<true>(m[0], m[1], a, grid, smem, s)
+                    : launch_fourier_t<false>(m[0], m[1], a, grid, smem, s);
 }
 
 }  // namespace dmk

@@ -144,7 +144,8 @@ struct ProbeFinalArgs {
 };
 
 // Launchers (return the launch error).
-cudaError_t launch_fourier(const void* tmap, const FourierArgs& a, int grid, size_t smem, cudaStream_t s);
+// tmaps: two CUtensorMap of the scratch ring (box of all modes, box of one mode)
+cudaError_t launch_fourier(const void* tmaps, const FourierArgs& a, int grid, size_t smem, cudaStream_t s);
 size_t fourier_smem_bytes(int N, int M, int bufs, int G);
 int fourier_occupancy(int N, size_t smem);
 int fourier_r2(int N);
