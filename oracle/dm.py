@@ -215,8 +215,15 @@ def rel_change(new, old):
 # One DM iteration.
 # --------------------------------------------------------------------------
 def dm_iteration(psi, probe, obj, pos, intensities, beta=0.8, delta_rel=1e-6,
-                 n_inner=1, update_probe=True):
+                 n_inner=1, update_probe=True, order="gauss-seidel"):
     """Eq. 3, then (Eq. 5, Eq. 4) x n_inner, then Eq. 6.
+
+    Eqs. 4 and 5 are written as simultaneous updates.  ``order`` picks how
+    they are taken:
+    - "gauss-seidel" (the default): the object from the current probe, then
+      the probe from the new object, n_inner times;
+    - "jacobi": both from the values the iteration started with, so the
+      probe uses the old object (n_inner must be 1).
 
     All inputs are left untouched.  Returns (psi, probe, obj, metrics) with
     metrics = {"eps_obj", "eps_probe" (list over modes), "fourier_err",
@@ -228,12 +235,17 @@ def dm_iteration(psi, probe, obj, pos, intensities, beta=0.8, delta_rel=1e-6,
     probe = np.asarray(probe, dtype=np.complex128)
     obj = np.asarray(obj, dtype=np.complex128)
     intensities = np.asarray(intensities, dtype=np.float64)
+    if order not in ("gauss-seidel", "jacobi"):
+        raise ValueError(f"unknown order {order!r}")
+    if order == "jacobi" and n_inner != 1:
+        raise ValueError("the Jacobi order takes one inner pass")
     psi_new, ef = fourier_update(psi, probe, obj, pos, intensities, beta)
     o_new, p_new = obj, probe
     for _ in range(max(1, n_inner)):
+        o_prev = o_new
         o_new = object_update(psi_new, p_new, o_new, pos, delta_rel)
         if update_probe:
-            p_new = probe_update(psi_new, p_new, o_new, pos, delta_rel)
+            p_new = probe_update(psi_new, p_new, o_prev if order == "jacobi" else o_new, pos, delta_rel)
     metrics = {
         "eps_obj": rel_change(o_new, obj),
         "eps_probe": [rel_change(p_new[k], probe[k]) for k in range(probe.shape[0])],
@@ -244,7 +256,7 @@ def dm_iteration(psi, probe, obj, pos, intensities, beta=0.8, delta_rel=1e-6,
 
 
 def reconstruct(probe0, obj0, pos, intensities, n_iter, beta=0.8, delta_rel=1e-6,
-                n_inner=1, probe_update_start=0, psi0=None):
+                n_inner=1, probe_update_start=0, psi0=None, order="gauss-seidel"):
     """Run ``n_iter`` iterations from the initial guesses.  The probe is held
     fixed for iterations t < probe_update_start.  Returns
     (psi, probe, obj, list of per-iteration metrics)."""
@@ -254,7 +266,7 @@ def reconstruct(probe0, obj0, pos, intensities, n_iter, beta=0.8, delta_rel=1e-6
     history = []
     for t in range(n_iter):
         psi, probe, obj, m = dm_iteration(psi, probe, obj, pos, intensities, beta, delta_rel,
-                                          n_inner, update_probe=(t >= probe_update_start))
+                                          n_inner, update_probe=(t >= probe_update_start), order=order)
         history.append(m)
     return psi, probe, obj, history
 

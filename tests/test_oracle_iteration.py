@@ -1,12 +1,13 @@
 """Pins for one whole oracle DM iteration (Eq. 3, Eq. 5, Eq. 4, Eq. 6).
 
 * fixed point: noise-free intensities of (P*, O*) with psi = P* O* are left
-  unchanged by one iteration;
+  unchanged by one iteration, in either update order;
 * gauges: a global phase on (O, psi) and the scalar ambiguity (cP, O/c);
 * modes: a unitary mixing of the probe modes commutes with the iteration,
   and an extra all-zero mode stays zero and changes nothing;
 * brute force: an independent loop-by-loop implementation written from the
-  equations (explicit DFT sums) on tiny inputs, single- and multi-mode;
+  equations (explicit DFT sums) on tiny inputs, single- and multi-mode, in
+  both update orders (the probe from the new object or from the old one);
 * metrics: Eq. 6 on a known perturbation, the Fourier error on data that is
   exactly four times the model intensity, and the exit-wave change (with the
   exit-wave update itself) on data equal to one or four times the model
@@ -54,8 +55,8 @@ def test_exact_solution_is_a_fixed_point():
     probe, obj, pos = small_state(rng, m=3)
     inten = model_intensities(probe, obj, pos)
     psi = dm.init_exit_waves(probe, obj, pos)
-    for beta in (0.8, 1.0):
-        psi1, p1, o1, m = dm.dm_iteration(psi, probe, obj, pos, inten, beta=beta, delta_rel=0.0)
+    for beta, order in ((0.8, "gauss-seidel"), (1.0, "gauss-seidel"), (0.8, "jacobi")):
+        psi1, p1, o1, m = dm.dm_iteration(psi, probe, obj, pos, inten, beta=beta, delta_rel=0.0, order=order)
         np.testing.assert_allclose(psi1, psi, rtol=0, atol=1e-12 * np.abs(psi).max())
         np.testing.assert_allclose(o1, obj, rtol=0, atol=1e-12 * np.abs(obj).max())
         np.testing.assert_allclose(p1, probe, rtol=0, atol=1e-12 * np.abs(probe).max())
@@ -134,7 +135,7 @@ def _dft(frame, sign):
     return out
 
 
-def loop_dm_iteration(psi, probe, obj, pos, inten, beta, delta_rel):
+def loop_dm_iteration(psi, probe, obj, pos, inten, beta, delta_rel, jacobi=False):
     J, M, N = len(psi), len(probe), len(probe[0])
     H, W = len(obj), len(obj[0])
     psi = [[[list(row) for row in psi[j][k]] for k in range(M)] for j in range(J)]
@@ -170,7 +171,7 @@ def loop_dm_iteration(psi, probe, obj, pos, inten, beta, delta_rel):
         r0, c0 = int(pos[j][0]), int(pos[j][1])
         for y in range(N):
             for x in range(N):
-                o = new_obj[r0 + y][c0 + x]
+                o = (obj if jacobi else new_obj)[r0 + y][c0 + x]
                 pden[y][x] += abs(o) ** 2
                 for k in range(M):
                     pnum[k][y][x] += o.conjugate() * new_psi[j][k][y][x]
@@ -190,9 +191,10 @@ def test_matches_independent_loop_implementation(m, n):
     psi = dm.init_exit_waves(probe, obj, pos) + 0.5 * rand_c(rng, (len(pos), m, n, n))
     inten = rng.uniform(0, 4, (len(pos), n, n))
     inten[1, 0, 0] = -1.0
-    for beta, dr in ((0.8, 1e-3), (1.0, 0.0)):
-        a = dm.dm_iteration(psi, probe, obj, pos, inten, beta=beta, delta_rel=dr)
-        b = loop_dm_iteration(psi.tolist(), probe.tolist(), obj.tolist(), pos.tolist(), inten.tolist(), beta, dr)
+    for beta, dr, order in ((0.8, 1e-3, "gauss-seidel"), (1.0, 0.0, "gauss-seidel"), (0.8, 1e-3, "jacobi")):
+        a = dm.dm_iteration(psi, probe, obj, pos, inten, beta=beta, delta_rel=dr, order=order)
+        b = loop_dm_iteration(psi.tolist(), probe.tolist(), obj.tolist(), pos.tolist(), inten.tolist(), beta, dr,
+                              jacobi=(order == "jacobi"))
         np.testing.assert_allclose(a[0], b[0], atol=1e-12)
         np.testing.assert_allclose(a[1], b[1], atol=1e-11)
         np.testing.assert_allclose(a[2], b[2], atol=1e-12)
@@ -266,3 +268,17 @@ def test_exit_wave_change_closed_form(scale):
     assert np.abs(psi_new - want).max() <= 1e-12 * np.abs(want).max()
     d = np.sqrt(np.sum(np.abs(want - psi) ** 2) / np.sum(np.abs(want) ** 2))
     assert m["eps_psi"] == pytest.approx(d, rel=1e-12)
+
+
+def test_update_orders_differ_only_in_the_probe():
+    # The two orders share Eq. 3 and Eq. 5; only the object Eq. 4 divides by
+    # differs, and a Jacobi order needs a single inner pass.
+    rng = np.random.default_rng(41)
+    psi, probe, obj, pos, inten = generic_inputs(rng, m=2)
+    gs = dm.dm_iteration(psi, probe, obj, pos, inten, order="gauss-seidel")
+    ja = dm.dm_iteration(psi, probe, obj, pos, inten, order="jacobi")
+    np.testing.assert_array_equal(gs[0], ja[0])
+    np.testing.assert_array_equal(gs[2], ja[2])
+    assert np.abs(gs[1] - ja[1]).max() > 1e-3 * np.abs(gs[1]).max()
+    with pytest.raises(ValueError):
+        dm.dm_iteration(psi, probe, obj, pos, inten, order="jacobi", n_inner=2)
