@@ -107,11 +107,23 @@ typedef struct dm_params {
                               /* other streams must be complete at dm_init)      */
   int64_t scratch_bytes;      /* L2-resident Fourier-step scratch; 0 = 96 MiB.   */
                               /* Smaller values mean smaller view chunks.        */
+  int32_t update_order;       /* DM_ORDER_GAUSS_SEIDEL (default) or DM_ORDER_JACOBI */
 } dm_params;
+
+/* Order of the overlap projection (Eqs. 4 and 5, written in the paper as
+ * simultaneous updates).  Gauss-Seidel: the object from the probe the Fourier
+ * step used, then each probe mode from the new object (n_inner passes).
+ * Jacobi: both from the values the iteration started with, so each probe mode
+ * divides by the old object; it requires n_inner = 1 (DM_EINVAL otherwise).
+ * With view shards (dm_probe_partials) the Jacobi order uses the object that
+ * was current before dm_object_apply. */
+#define DM_ORDER_GAUSS_SEIDEL 0
+#define DM_ORDER_JACOBI 1
 
 /* Fill p with the defaults: beta 0.8, n_inner 1, probe_update_start 0,
  * denom_floor_rel 1e-6, mem_kind DM_HOST, no allocator, NULL stream,
- * default scratch; the sizes are zeroed and must be set by the caller. */
+ * default scratch, Gauss-Seidel order; the sizes are zeroed and must be set
+ * by the caller. */
 void dm_params_default(dm_params* p);
 
 /* Create a context on the current CUDA device: validate the parameters,

@@ -584,6 +584,10 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   if (p->mem_kind != DM_HOST && p->mem_kind != DM_DEVICE) return fail(nullptr, DM_EINVAL, "bad mem_kind");
   if ((p->alloc == nullptr) != (p->free == nullptr)) return fail(nullptr, DM_EINVAL, "alloc and free go together");
   if (p->scratch_bytes < 0) return fail(nullptr, DM_EINVAL, "scratch_bytes must be >= 0");
+  if (p->update_order != DM_ORDER_GAUSS_SEIDEL && p->update_order != DM_ORDER_JACOBI)
+    return fail(nullptr, DM_EINVAL, "unknown update_order");
+  if (p->update_order == DM_ORDER_JACOBI && p->n_inner != 1)
+    return fail(nullptr, DM_EINVAL, "the Jacobi order takes n_inner = 1");
   if (p->mem_kind == DM_HOST) {
     for (int j = 0; j < p->views; ++j) {
       const int r = positions[2 * j], q = positions[2 * j + 1];
@@ -710,6 +714,12 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
 
 namespace {
 
+// The object Eq. 4 divides by within an iteration, after the object update
+// wrote obj[cur_O ^ 1]: the new object (Gauss-Seidel) or the old one (Jacobi).
+const float2* probe_object(const dm_ctx* c) {
+  return c->obj[c->p.update_order == DM_ORDER_JACOBI ? c->cur_O : c->cur_O ^ 1];
+}
+
 // Every launch of one iteration (Eq. 3, then Eq. 5 and Eq. 4 n_inner times,
 // then Eq. 6), enqueued on the context's stream; no host state changes.
 int enqueue_iteration(dm_ctx* c, bool upd) {
@@ -722,7 +732,7 @@ int enqueue_iteration(dm_ctx* c, bool upd) {
     }
     if ((rc = run_object(c))) return rc;
     if (!upd) break;  // later passes would repeat the same object update
-    if ((rc = run_probe(c, c->obj[c->cur_O ^ 1]))) return rc;
+    if ((rc = run_probe(c, probe_object(c)))) return rc;
   }
   return run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd, true);
 }
@@ -961,7 +971,7 @@ int enqueue_batch_iteration(dm_batch* b) {
       }
       if (rc == DM_OK) rc = run_object(c);
       if (!upd) break;
-      if (rc == DM_OK) rc = run_probe(c, c->obj[c->cur_O ^ 1]);
+      if (rc == DM_OK) rc = run_probe(c, probe_object(c));
     }
     if (rc == DM_OK) rc = run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd, false);
     c->stream = own;
@@ -1165,7 +1175,8 @@ int dm_probe_partials(dm_ctx* c, double* num, double* den, int32_t mem_kind) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!num || !den || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad output");
-  if ((rc = run_probe_sums(c, c->obj[c->cur_O]))) return rc;
+  // after dm_object_apply the new object is current; Jacobi takes the old one
+  if ((rc = run_probe_sums(c, c->obj[c->p.update_order == DM_ORDER_JACOBI ? c->cur_O ^ 1 : c->cur_O]))) return rc;
   const size_t nn = (size_t)c->N * c->N;
   if ((rc = copy_out(c, num, c->num_sum, 2 * (size_t)c->M * nn * sizeof(double), mem_kind))) return rc;
   if ((rc = copy_out(c, den, c->den_sum, nn * sizeof(double), mem_kind))) return rc;

@@ -24,6 +24,7 @@ DM_OK, DM_EINVAL, DM_ENOMEM, DM_ECUDA, DM_ENONFINITE, DM_ETIMEOUT = 0, -1, -2, -
 DM_HOST, DM_DEVICE = 0, 1
 DM_STEP_FOURIER, DM_STEP_OBJECT, DM_STEP_PROBE = 0, 1, 2
 DM_DFT_FP32, DM_DFT_BF16X3 = 0, 1
+DM_ORDER_GAUSS_SEIDEL, DM_ORDER_JACOBI = 0, 1
 (DM_KERNEL_FOURIER, DM_KERNEL_OBJECT_GATHER, DM_KERNEL_OBJECT_FINAL, DM_KERNEL_PROBE_PARTIAL,
  DM_KERNEL_PROBE_FINAL, DM_KERNEL_METRICS, DM_KERNEL_OTHER, DM_KERNEL_COUNT) = range(8)
 
@@ -41,6 +42,7 @@ class dm_params(ctypes.Structure):
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
         ("stream", ctypes.c_void_p),
         ("scratch_bytes", ctypes.c_int64),
+        ("update_order", ctypes.c_int32),
     ]
 
 

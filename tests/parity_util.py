@@ -34,12 +34,13 @@ def case(n, modes, grid, step, obj, seed, jitter=1, probe="hg", fwhm=None, photo
 
 
 def run_gpu(s, p0, o0, psi0, n_iter=1, beta=0.8, delta_rel=1e-6, n_inner=1, probe_update_start=0,
-            scratch_bytes=0, use_torch_allocator=None):
+            scratch_bytes=0, use_torch_allocator=None, order="gauss-seidel"):
     from paper_1808_10375_gb300 import dm
     h, w = s.obj_shape
     params = dm.dm_params_default(n=s.n, modes=s.modes, views=s.views, obj_h=h, obj_w=w, beta=beta,
                                   denom_floor_rel=delta_rel, n_inner=n_inner,
-                                  probe_update_start=probe_update_start, scratch_bytes=scratch_bytes)
+                                  probe_update_start=probe_update_start, scratch_bytes=scratch_bytes,
+                                  update_order=dm.DM_ORDER_JACOBI if order == "jacobi" else dm.DM_ORDER_GAUSS_SEIDEL)
     ctx = dm.dm_init(params, s.pos, s.intensities, p0, o0, use_torch_allocator=use_torch_allocator)
     if psi0 is not None:
         dm.dm_set_exit_waves(ctx, psi0)
@@ -50,7 +51,8 @@ def run_gpu(s, p0, o0, psi0, n_iter=1, beta=0.8, delta_rel=1e-6, n_inner=1, prob
     return out
 
 
-def run_oracle(s, p0, o0, psi0, n_iter=1, beta=0.8, delta_rel=1e-6, n_inner=1, probe_update_start=0):
+def run_oracle(s, p0, o0, psi0, n_iter=1, beta=0.8, delta_rel=1e-6, n_inner=1, probe_update_start=0,
+               order="gauss-seidel"):
     psi = psi0.astype(np.complex128) if psi0 is not None else odm.init_exit_waves(
         p0.astype(np.complex128), o0.astype(np.complex128), s.pos)
     probe = p0.astype(np.complex128)
@@ -59,7 +61,7 @@ def run_oracle(s, p0, o0, psi0, n_iter=1, beta=0.8, delta_rel=1e-6, n_inner=1, p
     hist = []
     for t in range(n_iter):
         psi, probe, obj, m = odm.dm_iteration(psi, probe, obj, s.pos, inten, beta, delta_rel, n_inner,
-                                              update_probe=(t >= probe_update_start))
+                                              update_probe=(t >= probe_update_start), order=order)
         hist.append(m)
     return dict(psi=psi, probe=probe, obj=obj, metrics=hist)
 

@@ -73,7 +73,8 @@ def _init_rc(lib, dm, **kw):
 @pytest.mark.parametrize("kw", [dict(n=48), dict(n=512), dict(modes=0), dict(modes=17), dict(views=0),
                                 dict(obj_h=8), dict(beta=1.5), dict(beta=float("nan")), dict(n_inner=0),
                                 dict(probe_update_start=-1), dict(denom_floor_rel=-1.0),
-                                dict(denom_floor_rel=float("inf")), dict(mem_kind=7), dict(scratch_bytes=-1)])
+                                dict(denom_floor_rel=float("inf")), dict(mem_kind=7), dict(scratch_bytes=-1),
+                                dict(update_order=2), dict(update_order=1, n_inner=2)])
 def test_invalid_params_rejected_without_gpu(lib, kw):
     from paper_1808_10375_gb300 import dm
     rc, h = _init_rc(lib, dm, **kw)

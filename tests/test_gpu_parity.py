@@ -165,3 +165,16 @@ def test_error_queries():
     dm.dm_sync(ctx)
     assert dm.dm_device_bytes(ctx) > 0
     dm.dm_free(ctx)
+
+
+@pytest.mark.parametrize("n,m,seed", [(64, 2, 51), (256, 3, 52)])
+def test_jacobi_order_matches_oracle(n, m, seed):
+    # Eqs. 4 and 5 as simultaneous updates: the probe divides by the object
+    # the iteration started with.
+    grid, step, obj = ((5, 5), 9, (110, 110)) if n == 64 else ((2, 2), 30, (290, 290))
+    s, p0, o0, psi0 = case(n, m, grid, step, obj, seed)
+    g = run_gpu(s, p0, o0, psi0, n_iter=2, order="jacobi")
+    o = run_oracle(s, p0, o0, psi0, n_iter=2, order="jacobi")
+    compare(g, o)
+    gs = run_oracle(s, p0, o0, psi0, n_iter=1)
+    assert rel_l2(o["probe"], gs["probe"]) > 10 * REL_L2   # the order shows in the result

@@ -17,14 +17,16 @@ def built():
     build.build()
 
 
-def run_sharded(s, p0, o0, psi0, shards, n_iter=1):
+def run_sharded(s, p0, o0, psi0, shards, n_iter=1, order="gauss-seidel"):
     from paper_1808_10375_gb300 import dm
     from paper_1808_10375_gb300.shard import sharded_iteration, split_views
     h, w = s.obj_shape
     ctxs, ranges = [], split_views(s.views, shards)
     for r in ranges:
         idx = np.arange(r.start, r.stop)
-        params = dm.dm_params_default(n=s.n, modes=s.modes, views=len(idx), obj_h=h, obj_w=w)
+        params = dm.dm_params_default(n=s.n, modes=s.modes, views=len(idx), obj_h=h, obj_w=w,
+                                      update_order=dm.DM_ORDER_JACOBI if order == "jacobi"
+                                      else dm.DM_ORDER_GAUSS_SEIDEL)
         c = dm.dm_init(params, s.pos[idx], s.intensities[idx], p0, o0)
         dm.dm_set_exit_waves(c, psi0[idx])
         ctxs.append(c)
@@ -89,3 +91,11 @@ def test_partials_sum_to_the_unsharded_partials():
     for i in range(5):
         tot = parts[0][i] + parts[1][i]
         assert rel_l2(tot, whole[i]) <= 1e-6, (i, rel_l2(tot, whole[i]))
+
+
+def test_sharded_jacobi_order_matches_oracle():
+    s, p0, o0, psi0 = case(64, 3, (5, 6), 9, (120, 130), 43)
+    sh = run_sharded(s, p0, o0, psi0, 2, n_iter=2, order="jacobi")
+    o = run_oracle(s, p0, o0, psi0, n_iter=2, order="jacobi")
+    compare(dict(psi=sh["psi"], obj=sh["objs"][0], probe=sh["probes"][0],
+                 metrics=[m[0] for m in sh["metrics"]]), o, tol=REL_L2)
