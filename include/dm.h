@@ -140,7 +140,9 @@ int dm_iterate(dm_ctx* ctx, int32_t n_iter);
 
 /* Enqueue one piece of an iteration (DM_STEP_*).  DM_STEP_OBJECT and
  * DM_STEP_PROBE replace the current object / probe; no metric is written
- * and the iteration counter does not move. */
+ * and the iteration counter does not move.  DM_STEP_PROBE always divides by
+ * the current object, whatever update_order says: the steps are the pieces
+ * of a Gauss-Seidel iteration. */
 int dm_run_step(dm_ctx* ctx, int32_t step);
 
 /* Copy the current object [H][W][2], probe [M][N][N][2] or exit waves
