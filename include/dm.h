@@ -178,6 +178,18 @@ int dm_get_error(dm_ctx* ctx, int32_t iter, double* eps_obj, double* eps_probe,
 int dm_set_psi_error(dm_ctx* ctx, int32_t enable);
 int dm_get_psi_error(dm_ctx* ctx, int32_t iter, double* eps_psi);
 
+/* Diagnostic for the failure path: runs the library's two bounded device
+ * waits on conditions that never become true (a counter spin-wait on a flag
+ * nothing raises, an mbarrier wait on a phase nothing completes), on the
+ * current device and its legacy default stream.  Each must give up after its
+ * limit (1 s) and set the timeout status, which is what makes a stalled
+ * Fourier step end with DM_ETIMEOUT instead of hanging.  Returns DM_OK when
+ * both gave up and flagged it and the device still runs work afterwards,
+ * DM_EINVAL if a wait did not give up as designed, DM_ECUDA on a CUDA error
+ * (message in dm_last_error(NULL)).  *elapsed_ms (if non-NULL) receives the
+ * device time of the test kernel (about 2000 ms).  Synchronises. */
+int dm_selftest_bounded_waits(double* elapsed_ms);
+
 /* Number of completed dm_iterate iterations. */
 int64_t dm_iterations_done(const dm_ctx* ctx);
 

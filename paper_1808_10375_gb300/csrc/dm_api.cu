@@ -1316,6 +1316,37 @@ int dm_get_psi_error(dm_ctx* c, int32_t iter, double* eps_psi) {
   return check_status(c);
 }
 
+int dm_selftest_bounded_waits(double* elapsed_ms) {
+  g_init_error.clear();
+  int* d = nullptr;   // [0] flag nothing raises, [1..2] status words, [3..4] wait results
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d), 5 * sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMalloc");
+  int h[5] = {0, 0, 0, 0, 0};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
+  e = cudaMemset(d, 0, 5 * sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+  if (e == cudaSuccess) e = dmk::launch_wait_selftest(d, d + 1, d + 3, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  // the context is still usable: a plain device operation after the waits
+  if (e == cudaSuccess) e = cudaMemset(d, 0, 5 * sizeof(int));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "bounded-wait self-test");
+  if (elapsed_ms) *elapsed_ms = ms;
+  const bool gave_up = h[3] == 0 && h[4] == 0;
+  const bool flagged = (h[1] & dmk::kStatusTimeout) && (h[2] & dmk::kStatusTimeout);
+  if (!gave_up || !flagged) return fail(nullptr, DM_EINVAL, "a bounded wait did not give up as designed");
+  return DM_OK;
+}
+
 int64_t dm_iterations_done(const dm_ctx* c) { return c ? c->iters : -1; }
 
 int dm_get_mode_power(dm_ctx* c, double* out) {

@@ -185,6 +185,8 @@ cudaError_t launch_metrics(const double* ef_part, long long n_ef, const double* 
                            int n_probe, int M, int probe_updated, const double* psi_part, long long n_psi,
                            double* ring, long long* iter, int* status, cudaStream_t s);
 cudaError_t launch_mode_power(const float2* probe, int N, int M, double* out, cudaStream_t s);
+// flag: one zeroed int; status: two zeroed ints; ok: two ints (see k_wait_selftest)
+cudaError_t launch_wait_selftest(const int* flag, int* status, int* ok, cudaStream_t s);
 
 // Batched 2-D DFT of 256 x 256 frames (dm_dft.cu): tables and limits once
 // per device, then the two row passes (precision 0 FP32, 1 split BF16 on the

@@ -509,9 +509,28 @@ __global__ void __launch_bounds__(kThreads) k_metrics(const double* ef_part, lon
   if (threadIdx.x == 0) *iter += 1;
 }
 
+// Self-test of the bounded device waits: a counter spin-wait on a flag that
+// nothing raises, and an mbarrier wait on a phase that nothing completes.
+// Each must give up after the wait limit and set kStatusTimeout in its own
+// status word; ok[i] records the wait's return value (0 = gave up).
+__global__ void k_wait_selftest(const int* flag, int* status, int* ok) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    ok[0] = spin_wait_geq(flag, 1, status) ? 1 : 0;
+    ok[1] = mbar_wait_bounded(&bar, 0u, status + 1) ? 1 : 0;   // no arrival: phase 0 never completes
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
+cudaError_t launch_wait_selftest(const int* flag, int* status, int* ok, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(flag, status, ok);
+  return cudaGetLastError();
+}
+
 static int grid_for(size_t work, int cap) {
   size_t g = (work + kThreads - 1) / kThreads;
   if (g < 1) g = 1;

@@ -54,7 +54,7 @@ class DMError(RuntimeError):
 
 EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_object", "dm_get_probe",
            "dm_get_exit_waves", "dm_set_exit_waves", "dm_set_object", "dm_set_probe", "dm_get_error",
-           "dm_set_psi_error", "dm_get_psi_error", "dm_iterations_done", "dm_get_mode_power", "dm_sync", "dm_set_timing", "dm_get_timing",
+           "dm_set_psi_error", "dm_get_psi_error", "dm_selftest_bounded_waits", "dm_iterations_done", "dm_get_mode_power", "dm_sync", "dm_set_timing", "dm_get_timing",
            "dm_kernel_name", "dm_device_bytes", "dm_free", "dm_last_error", "dm_probe_update_static",
            "dm_object_partials", "dm_object_apply", "dm_probe_partials", "dm_probe_apply",
            "dm_fourier_error_partials", "dm_finish_iteration", "dm_set_graph", "dm_autotune",
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
         "dm_set_probe": (ctypes.c_int, [vp, vp, i32]),
         "dm_get_error": (ctypes.c_int, [vp, i32, dp, dp, dp]),
         "dm_set_psi_error": (ctypes.c_int, [vp, i32]),
+        "dm_selftest_bounded_waits": (ctypes.c_int, [dp]),
         "dm_get_psi_error": (ctypes.c_int, [vp, i32, dp]),
         "dm_iterations_done": (i64, [vp]),
         "dm_get_mode_power": (ctypes.c_int, [vp, dp]),
@@ -579,6 +580,16 @@ def dm_get_psi_error(ctx: Context, iteration: int = -1) -> float:
     out = ctypes.c_double()
     _check(load().dm_get_psi_error(ctx.handle, int(iteration), ctypes.byref(out)), ctx)
     return out.value
+
+
+def dm_selftest_bounded_waits() -> float:
+    """Make the library's bounded device waits run out (see dm.h); returns
+    the test kernel's device time in ms, raises if a wait did not give up."""
+    ms = ctypes.c_double()
+    rc = load().dm_selftest_bounded_waits(ctypes.byref(ms))
+    if rc != DM_OK:
+        raise DMError(rc, (load().dm_last_error(None) or b"").decode())
+    return ms.value
 
 
 def dm_iterations_done(ctx: Context) -> int:

@@ -80,3 +80,16 @@ def test_contexts_of_one_frame_size_with_different_plans():
                  metrics=[dm.dm_get_error(c, 0)])
         dm.dm_free(c)
         compare(g, run_oracle(s, p0, o0, psi0))
+
+
+def test_bounded_waits_give_up_and_the_device_stays_usable():
+    """The failure path without a fault: a counter wait on a flag that nothing
+    raises and an mbarrier wait on a phase that nothing completes each give
+    up after their 1 s limit and set the timeout status (what turns a stalled
+    Fourier step into DM_ETIMEOUT); afterwards a whole iteration still runs
+    and matches the oracle."""
+    from paper_1808_10375_gb300 import dm
+    ms = dm.dm_selftest_bounded_waits()
+    assert 1900.0 <= ms <= 20000.0, ms
+    s, p0, o0, psi0 = case(32, 2, (3, 3), 6, (50, 50), 61)
+    compare(run_gpu(s, p0, o0, psi0), run_oracle(s, p0, o0, psi0))
