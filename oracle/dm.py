@@ -255,22 +255,6 @@ def dm_iteration(psi, probe, obj, pos, intensities, beta=0.8, delta_rel=1e-6,
     return psi_new, p_new, o_new, metrics
 
 
-def reconstruct(probe0, obj0, pos, intensities, n_iter, beta=0.8, delta_rel=1e-6,
-                n_inner=1, probe_update_start=0, psi0=None, order="gauss-seidel"):
-    """Run ``n_iter`` iterations from the initial guesses.  The probe is held
-    fixed for iterations t < probe_update_start.  Returns
-    (psi, probe, obj, list of per-iteration metrics)."""
-    probe = np.asarray(probe0, dtype=np.complex128)
-    obj = np.asarray(obj0, dtype=np.complex128)
-    psi = init_exit_waves(probe, obj, pos) if psi0 is None else np.asarray(psi0, np.complex128)
-    history = []
-    for t in range(n_iter):
-        psi, probe, obj, m = dm_iteration(psi, probe, obj, pos, intensities, beta, delta_rel,
-                                          n_inner, update_probe=(t >= probe_update_start), order=order)
-        history.append(m)
-    return psi, probe, obj, history
-
-
 def mode_power(probe):
     """sum_u |P_k(u)|^2 for every mode (the per-mode contribution used to
     choose the number of modes, Sec. II)."""
