@@ -273,13 +273,16 @@ size_t dm_device_bytes(const dm_ctx* ctx);
  * array inside the library (held by every GPU that loads the library until
  * the process exits), which bounds the size: about (24 M + 20) N^2 bytes
  * must fit in 16 MiB (N = 256 allows up to 9 modes).  Larger sizes return
- * DM_EINVAL.  The first call on a device looks up the array's address; make
- * it before any stream capture.  All calls share the array: calls that
- * overlap on the GPU race, so order them on one stream.  The positions are
- * checked on the device first, so the call synchronises `stream`; the
- * update itself is left enqueued on `stream`.  Errors: DM_EINVAL (sizes,
- * NULL pointers, a footprint outside the object), DM_ECUDA; the message is
- * in dm_last_error(NULL). */
+ * DM_EINVAL.  The array's address on the current device is looked up on
+ * every call.  All calls share the array: calls that overlap on the GPU
+ * race, so order them on one stream.  The positions are checked on the
+ * device before the update and a status word is read after it, so the call
+ * synchronises `stream` and returns once probe_out holds the result; on a
+ * stream that is being captured into a graph it returns DM_EINVAL and
+ * enqueues nothing.  Errors: DM_EINVAL (sizes, NULL pointers, a footprint
+ * outside the object, a capturing stream), DM_ETIMEOUT (a bounded device
+ * wait of this call's update expired; probe_out is then not valid),
+ * DM_ECUDA; the message is in dm_last_error(NULL). */
 int dm_probe_update_static(const float* psi, const float* object, const int32_t* positions,
                            const float* probe_in, float* probe_out, int32_t n, int32_t modes,
                            int32_t views, int32_t obj_h, int32_t obj_w, double denom_floor_rel,
@@ -307,11 +310,16 @@ int dm_probe_update_static(const float* psi, const float* object, const int32_t*
  * dm_object_partials: numerator and denominator of Eq. 5 over this
  *   context's views, with the probe the Fourier step used:
  *   num [H][W] complex (float pairs) = sum_jk conj(P_k(r-r_j)) psi_j^k(r-r_j),
- *   den [H][W] float = sum_jk |P_k(r-r_j)|^2 (0 where no view of the shard
- *   covers r).  Needs the Fourier step of this iteration to have run.
- * dm_object_apply: the object update from the summed num, den (same layouts):
- *   O = num / (den + delta), delta = denom_floor_rel * max(den); pixels with
- *   den = 0 keep their value.  It becomes the current object.
+ *   summed in FP32 as the unsharded gather sums it;
+ *   den [H][W] double = sum_jk |P_k(r-r_j)|^2 (0 where no view of the shard
+ *   covers r), summed in FP32 over blocks of 32 views and in FP64 across
+ *   blocks, returned without rounding to float.  Needs the Fourier step of
+ *   this iteration to have run.
+ * dm_object_apply: the object update from the sums over all shards, held
+ *   in FP64: num [H][W][2] double, den [H][W] double.  O = num / (den +
+ *   delta), delta = denom_floor_rel * max(den), formed in FP64 and rounded
+ *   to float once; pixels with den = 0 keep their value.  It becomes the
+ *   current object.
  * dm_probe_partials: numerator and denominator of Eq. 4 over this context's
  *   views with the current object, in FP64: num [M][N][N][2] double,
  *   den [N][N] double = sum_j |O(r_j+u)|^2.
@@ -326,8 +334,8 @@ int dm_probe_update_static(const float* psi, const float* object, const int32_t*
  *   `sums`, a host array of 2) and counts the iteration.
  * num/den pointers follow mem_kind; the caller owns every buffer.  Errors:
  * DM_EINVAL (NULL pointers, bad mem_kind), DM_ECUDA. */
-int dm_object_partials(dm_ctx* ctx, float* num, float* den, int32_t mem_kind);
-int dm_object_apply(dm_ctx* ctx, const float* num, const float* den, int32_t mem_kind);
+int dm_object_partials(dm_ctx* ctx, float* num, double* den, int32_t mem_kind);
+int dm_object_apply(dm_ctx* ctx, const double* num, const double* den, int32_t mem_kind);
 int dm_probe_partials(dm_ctx* ctx, double* num, double* den, int32_t mem_kind);
 int dm_probe_apply(dm_ctx* ctx, const double* num, const double* den, int32_t mem_kind);
 int dm_fourier_error_partials(dm_ctx* ctx, double* sums);

@@ -64,6 +64,9 @@ struct dm_ctx {
   float* istrip = nullptr;
   float* p2 = nullptr;
   float* den_O = nullptr;
+  double* den64_O = nullptr;    // [H][W] FP64 denominator (view shards; allocated on first use)
+  double2* num64_O = nullptr;   // [H][W] summed FP64 numerator given to dm_object_apply
+  unsigned long long* dmax64_O = nullptr;
   int2* pos = nullptr;
   int* counters = nullptr;
   int* stage_off = nullptr;
@@ -456,12 +459,12 @@ int run_fourier(dm_ctx* c) {
 
 // Eq. 5, part 1: numerator and denominator over the context's views from
 // the current object sources (num_O, den_O, and the maximum of den_O).
-int run_object_gather(dm_ctx* c) {
+int run_object_gather(dm_ctx* c, double* den64 = nullptr) {
   DM_CUDA(c, cudaMemsetAsync(c->dmax_O, 0, sizeof(unsigned), c->stream));
   dmk::ObjGatherArgs g{};
   g.N = c->N; g.J = c->J; g.H = c->H; g.W = c->W; g.tiles_x = c->tiles_x;
   g.pos = c->pos; g.tile_ptr = c->tile_ptr; g.tile_views = c->tile_views; g.p2 = c->p2;
-  g.num = c->num_O; g.den = c->den_O; g.den_max_bits = c->dmax_O; g.status = c->status;
+  g.num = c->num_O; g.den = c->den_O; g.den64 = den64; g.den_max_bits = c->dmax_O; g.status = c->status;
   Timed t(c, DM_KERNEL_OBJECT_GATHER);
   DM_CUDA(c, dmk::launch_obj_gather(&c->tmap_c, g, c->tiles_x * c->tiles_y, c->stream));
   return DM_OK;
@@ -1145,27 +1148,38 @@ int dm_run_step(dm_ctx* c, int32_t step) {
   }
 }
 
-int dm_object_partials(dm_ctx* c, float* num, float* den, int32_t mem_kind) {
+int dm_object_partials(dm_ctx* c, float* num, double* den, int32_t mem_kind) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!num || !den || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad output");
-  if ((rc = run_object_gather(c))) return rc;
   const size_t hw = (size_t)c->H * c->W;
+  if (!c->den64_O && (rc = alloc_n(c, &c->den64_O, hw))) return rc;
+  if ((rc = run_object_gather(c, c->den64_O))) return rc;
   if ((rc = copy_out(c, num, c->num_O, hw * sizeof(float2), mem_kind))) return rc;
-  if ((rc = copy_out(c, den, c->den_O, hw * sizeof(float), mem_kind))) return rc;
+  if ((rc = copy_out(c, den, c->den64_O, hw * sizeof(double), mem_kind))) return rc;
   return check_status(c);
 }
 
-int dm_object_apply(dm_ctx* c, const float* num, const float* den, int32_t mem_kind) {
+int dm_object_apply(dm_ctx* c, const double* num, const double* den, int32_t mem_kind) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!num || !den || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad input");
   const size_t hw = (size_t)c->H * c->W;
-  if ((rc = copy_in(c, c->num_O, num, hw * sizeof(float2), mem_kind))) return rc;
-  if ((rc = copy_in(c, c->den_O, den, hw * sizeof(float), mem_kind))) return rc;
-  DM_CUDA(c, cudaMemsetAsync(c->dmax_O, 0, sizeof(unsigned), c->stream));
-  DM_CUDA(c, dmk::launch_max_f32(c->den_O, hw, c->dmax_O, c->stream));
-  if ((rc = run_object_final(c))) return rc;
+  if (!c->den64_O && (rc = alloc_n(c, &c->den64_O, hw))) return rc;
+  if (!c->num64_O && (rc = alloc_n(c, &c->num64_O, hw))) return rc;
+  if (!c->dmax64_O && (rc = alloc_n(c, &c->dmax64_O, 1))) return rc;
+  if ((rc = copy_in(c, c->num64_O, num, hw * sizeof(double2), mem_kind))) return rc;
+  if ((rc = copy_in(c, c->den64_O, den, hw * sizeof(double), mem_kind))) return rc;
+  DM_CUDA(c, cudaMemsetAsync(c->dmax64_O, 0, sizeof(unsigned long long), c->stream));
+  DM_CUDA(c, dmk::launch_max_f64(c->den64_O, hw, c->dmax64_O, c->stream));
+  dmk::ObjFinal64Args f{};
+  f.H = c->H; f.W = c->W; f.delta_rel = c->p.denom_floor_rel;
+  f.num = c->num64_O; f.den = c->den64_O; f.den_max_bits = c->dmax64_O;
+  f.o_start = c->obj[c->cur_O]; f.o_new = c->obj[c->cur_O ^ 1]; f.part = c->obj_part;
+  {
+    Timed t(c, DM_KERNEL_OBJECT_FINAL);
+    DM_CUDA(c, dmk::launch_obj_final64(f, c->obj_final_blocks, c->stream));
+  }
   c->cur_O ^= 1;
   DM_CUDA(c, cudaStreamSynchronize(c->stream));   // the inputs may be host temporaries of the caller
   return DM_OK;

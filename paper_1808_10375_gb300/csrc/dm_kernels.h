@@ -97,6 +97,7 @@ struct ObjGatherArgs {
   const float* p2;         // [N][N] sum_k |P_k|^2
   float2* num;             // [H][W]
   float* den;              // [H][W]
+  double* den64;           // [H][W] the denominator before its float rounding (null: not written)
   unsigned* den_max_bits;  // max over the object (float bits, den >= 0)
   int* status;
 };
@@ -111,6 +112,21 @@ struct ObjFinalArgs {
   float2* o_new;
   double* part;            // [blocks][2]: sum |O_new - O_start|^2, sum |O_new|^2
 };
+
+// The object division from numerator and denominator sums held in FP64 (the
+// view-sharded path, whose sums are added over shards in FP64): O = num /
+// (den + delta) with delta = delta_rel * max(den), rounded to float once.
+struct ObjFinal64Args {
+  int H, W;
+  double delta_rel;
+  const double2* num;                  // [H][W]
+  const double* den;                   // [H][W]
+  const unsigned long long* den_max_bits;  // max of den (bits of the float-rounded value)
+  const float2* o_start;
+  float2* o_new;
+  double* part;            // [blocks][2] as ObjFinalArgs
+};
+cudaError_t launch_obj_final64(const ObjFinal64Args& a, int blocks, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Probe update (Eq. 4): per-view-group partial sums, then a fixed-order

@@ -13,22 +13,26 @@
 // Notes for users:
 //  * The array (kStaticScratchBytes = 16 MiB) is part of the library image:
 //    every GPU that loads the library holds it until the process exits.
-//  * Its device address is looked up once per device, on the first call made
-//    with that device current (cudaGetSymbolAddress); make that first call
-//    before any stream capture.
+//  * Its device address is looked up on every call, with the caller's device
+//    current (cudaGetSymbolAddress allocates nothing), so a device whose
+//    primary context was reset in between gets the array's new address.
 //  * All calls share the array.  Calls whose work overlaps on the GPU (for
 //    example on two streams without ordering) race on it and give wrong
 //    results; order them on one stream.
 //  * The array keeps the last call's contents; everything a call needs to
-//    start at zero is cleared by the call itself.  Its first word is a status
-//    word: a bounded device wait that expired during a call (which leaves
-//    that call's result wrong rather than hanging the GPU) is reported as
-//    DM_ETIMEOUT by the next call on the same stream, which clears it.
+//    start at zero is cleared by the call itself.
+//  * The call checks the positions on the device before any kernel reads the
+//    object, and reads a status word after the update, so it synchronises
+//    `stream` twice and returns only once the new probe is in probe_out.  It
+//    cannot be recorded into a CUDA graph: on a capturing stream it returns
+//    DM_EINVAL without enqueuing anything.
+//  * A bounded device wait that expired during the update (which leaves the
+//    result wrong rather than hanging the GPU) is returned by that same call
+//    as DM_ETIMEOUT; probe_out then holds no valid result.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <numeric>
 #include <string>
 
@@ -38,12 +42,8 @@
 namespace {
 
 constexpr size_t kStaticScratchBytes = 16ull << 20;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
-
-std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
 
 // Failures are reported through dm_last_error(NULL).
 int fail(int code, const std::string& msg) {
@@ -88,22 +88,22 @@ extern "C" int dm_probe_update_static(const float* psi, const float* object, con
     return fail(DM_EINVAL, "n * n * modes too large for the 16 MiB static scratch (needs " +
                                std::to_string(fixed + per_group) + " bytes)");
 
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return fail(DM_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(DM_EINVAL, "dm_probe_update_static synchronises its stream and cannot be captured in a graph");
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(DM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return fail(DM_EINVAL, "device index out of range");
-  unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-      void* addr = nullptr;
-      e = cudaGetSymbolAddress(&addr, g_static_scratch);
-      if (e != cudaSuccess || !addr)
-        return fail(DM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_scratch_addr[dev] = addr;
-    }
-    base = static_cast<unsigned char*>(g_scratch_addr[dev]);
-  }
+  // the host-side name of the array is not a device address: ask the runtime
+  // for the array's address on the current device, on every call
+  void* addr = nullptr;
+  e = cudaGetSymbolAddress(&addr, g_static_scratch);
+  if (e != cudaSuccess || !addr)
+    return fail(DM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  unsigned char* base = static_cast<unsigned char*>(addr);
 
   int num_sms = 0;
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -124,24 +124,19 @@ extern "C" int dm_probe_update_static(const float* psi, const float* object, con
   float2* part_num = reinterpret_cast<float2*>(carve((size_t)groups * modes * nn * sizeof(float2)));
   double* part_den = reinterpret_cast<double*>(carve((size_t)groups * nn * sizeof(double)));
 
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int2* pos = reinterpret_cast<const int2*>(positions);
-  // positions come from device memory: check them before any kernel reads the object
-  if ((e = cudaMemsetAsync(bad, 0, sizeof(int), s)) != cudaSuccess) return fail(DM_ECUDA, cudaGetErrorString(e));
+  // positions come from device memory: check them before any kernel reads the
+  // object; the status word starts at zero for this call's bounded waits
+  if ((e = cudaMemsetAsync(bad, 0, sizeof(int), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(status, 0, sizeof(int), s)) != cudaSuccess)
+    return fail(DM_ECUDA, cudaGetErrorString(e));
   k_check_positions<<<std::max(1, std::min(1024, (views + 255) / 256)), 256, 0, s>>>(pos, views, n, obj_h, obj_w, bad);
   int hbad = 0;
-  if ((e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+  if ((e = cudaGetLastError()) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return fail(DM_ECUDA, cudaGetErrorString(e));
   if (hbad) return fail(DM_EINVAL, "a footprint lies outside the object");
-  int hstatus = 0;
-  if ((e = cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(s)) != cudaSuccess)
-    return fail(DM_ECUDA, cudaGetErrorString(e));
-  if (hstatus & dmk::kStatusTimeout) {
-    cudaMemsetAsync(status, 0, sizeof(int), s);
-    return fail(DM_ETIMEOUT, "a bounded device wait of the previous call expired; its result is not valid");
-  }
 
   dmk::ProbePartialArgs a{};
   a.N = n; a.M = modes; a.J = views; a.H = obj_h; a.W = obj_w; a.groups = groups;
@@ -162,5 +157,11 @@ extern "C" int dm_probe_update_static(const float* psi, const float* object, con
   f.p2 = p2; f.num_sum = num_sum; f.den_sum = den_sum; f.den_max_bits = dmax; f.part = part;
   int blocks = 0;
   if ((e = dmk::launch_probe_final(f, s, &blocks)) != cudaSuccess) return fail(DM_ECUDA, cudaGetErrorString(e));
+  int hstatus = 0;
+  if ((e = cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return fail(DM_ECUDA, cudaGetErrorString(e));
+  if (hstatus & dmk::kStatusTimeout)
+    return fail(DM_ETIMEOUT, "a bounded device wait of the probe update expired; probe_out is not valid");
   return DM_OK;
 }

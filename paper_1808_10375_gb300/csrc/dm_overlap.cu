@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_obj_gather(const __grid_constant__
       const float d = (float)den64[m];
       a.num[(size_t)r * a.W + c] = num[m];
       a.den[(size_t)r * a.W + c] = d;
+      if (a.den64) a.den64[(size_t)r * a.W + c] = den64[m];
       lmax = fmaxf(lmax, d);
     }
   }
@@ -154,6 +155,35 @@ __global__ void __launch_bounds__(kThreads) k_obj_final(const ObjFinalArgs a) {
       const float2 nm = a.num[i];
       const float dd = den + delta;
       on = make_float2(nm.x / dd, nm.y / dd);
+    }
+    a.o_new[i] = on;
+    const float2 df = csub(on, o0);
+    d2 += (double)df.x * df.x + (double)df.y * df.y;
+    n2 += (double)on.x * on.x + (double)on.y * on.y;
+  }
+  d2 = block_sum(d2, sh);
+  n2 = block_sum(n2, sh);
+  if (threadIdx.x == 0) {
+    a.part[2 * blockIdx.x] = d2;
+    a.part[2 * blockIdx.x + 1] = n2;
+  }
+}
+
+// The same division from sums held in FP64 (view shards): the quotient is
+// formed in FP64 and rounded to float once.
+__global__ void __launch_bounds__(kThreads) k_obj_final64(const ObjFinal64Args a) {
+  __shared__ double sh[kThreads / 32];
+  const double delta = a.delta_rel * __longlong_as_double((long long)*a.den_max_bits);
+  const size_t n = (size_t)a.H * a.W;
+  double d2 = 0.0, n2 = 0.0;
+  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kThreads) {
+    const double den = a.den[i];
+    const float2 o0 = a.o_start[i];
+    float2 on = o0;
+    if (den > 0.0) {
+      const double2 nm = a.num[i];
+      const double dd = den + delta;
+      on = make_float2((float)(nm.x / dd), (float)(nm.y / dd));
     }
     a.o_new[i] = on;
     const float2 df = csub(on, o0);
@@ -544,6 +574,11 @@ cudaError_t launch_obj_gather(const void* tmap, const ObjGatherArgs& a, int ntil
 
 cudaError_t launch_obj_final(const ObjFinalArgs& a, int blocks, cudaStream_t s) {
   k_obj_final<<<blocks, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_obj_final64(const ObjFinal64Args& a, int blocks, cudaStream_t s) {
+  k_obj_final64<<<blocks, kThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -493,13 +493,15 @@ def _buf(x, shape, np_dtype, device):
     if x is None:
         if device:
             import torch
-            tdt = {np.float32: torch.float32, np.float64: torch.float64, np.complex64: torch.complex64}[np_dtype]
+            tdt = {np.float32: torch.float32, np.float64: torch.float64, np.complex64: torch.complex64,
+                   np.complex128: torch.complex128}[np_dtype]
             x = torch.empty(shape, dtype=tdt, device="cuda")
         else:
             x = np.empty(shape, dtype=np_dtype)
     if _is_torch(x):
         import torch
-        tdt = {np.float32: torch.float32, np.float64: torch.float64, np.complex64: torch.complex64}[np_dtype]
+        tdt = {np.float32: torch.float32, np.float64: torch.float64, np.complex64: torch.complex64,
+                   np.complex128: torch.complex128}[np_dtype]
         if x.dtype != tdt or not x.is_contiguous() or tuple(x.shape) != tuple(shape):
             raise ValueError(f"expected a contiguous {tdt} tensor of shape {shape}")
         return x, x.data_ptr(), (DM_DEVICE if x.is_cuda else DM_HOST)
@@ -509,10 +511,10 @@ def _buf(x, shape, np_dtype, device):
 
 
 def dm_object_partials(ctx: Context, num=None, den=None, device=False):
-    """(num [H][W] complex64, den [H][W] float32) of Eq. 5 over the context's views."""
+    """(num [H][W] complex64, den [H][W] float64) of Eq. 5 over the context's views."""
     p = ctx.params
     num, pn, mk = _buf(num, (p.obj_h, p.obj_w), np.complex64, device)
-    den, pd, mk2 = _buf(den, (p.obj_h, p.obj_w), np.float32, device)
+    den, pd, mk2 = _buf(den, (p.obj_h, p.obj_w), np.float64, device)
     if mk != mk2:
         raise ValueError("num and den must both be host or both be device buffers")
     _check(load().dm_object_partials(ctx.handle, pn, pd, mk), ctx)
@@ -520,9 +522,11 @@ def dm_object_partials(ctx: Context, num=None, den=None, device=False):
 
 
 def dm_object_apply(ctx: Context, num, den):
+    """Eq. 5 from numerator and denominator sums over all shards, in FP64:
+    num [H][W] complex128, den [H][W] float64."""
     p = ctx.params
-    num, pn, mk = _buf(num, (p.obj_h, p.obj_w), np.complex64, False)
-    den, pd, mk2 = _buf(den, (p.obj_h, p.obj_w), np.float32, False)
+    num, pn, mk = _buf(num, (p.obj_h, p.obj_w), np.complex128, False)
+    den, pd, mk2 = _buf(den, (p.obj_h, p.obj_w), np.float64, False)
     if mk != mk2:
         raise ValueError("num and den must both be host or both be device buffers")
     _check(load().dm_object_apply(ctx.handle, pn, pd, mk), ctx)
@@ -638,21 +642,55 @@ def dm_last_error(ctx: Context | None = None) -> str:
     return (load().dm_last_error(ctx.handle if ctx is not None else None) or b"").decode()
 
 
+def _static_probe_args(psi, obj, positions, probe_in, probe_out):
+    """Shapes (J, M, N, H, W) of dm_probe_update_static's tensors after
+    checking their types, layouts and shapes (ValueError on a mismatch)."""
+    import torch
+    names = ("psi", "obj", "positions", "probe_in", "probe_out")
+    want = (torch.complex64, torch.complex64, torch.int32, torch.complex64, torch.complex64)
+    dims = (4, 2, 2, 3, 3)
+    for name, t, dt, nd in zip(names, (psi, obj, positions, probe_in, probe_out), want, dims):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, not {t.dtype}")
+        if t.dim() != nd:
+            raise ValueError(f"{name} must have {nd} dimensions, not {t.dim()}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    j, m, n, n2 = psi.shape
+    h, w = obj.shape
+    if n2 != n:
+        raise ValueError("psi frames must be square")
+    if tuple(positions.shape) != (j, 2):
+        raise ValueError(f"positions must be [{j}, 2]")
+    for name, t in (("probe_in", probe_in), ("probe_out", probe_out)):
+        if tuple(t.shape) != (m, n, n):
+            raise ValueError(f"{name} must be [{m}, {n}, {n}]")
+    if h < n or w < n:
+        raise ValueError("the object must be at least N x N")
+    for name, t in zip(names, (psi, obj, positions, probe_in, probe_out)):
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+    dev = psi.device
+    if any(t.device != dev for t in (obj, positions, probe_in, probe_out)):
+        raise ValueError("all tensors must be on the same device")
+    return j, m, n, h, w
+
+
 def dm_probe_update_static(psi, obj, positions, probe_in, probe_out, denom_floor_rel=1e-6, stream=None):
     """Probe update (Eq. 4) that allocates no device memory: for callers that
     cannot call cudaMalloc (the C call's comment in include/dm.h has the
-    details and the size limit).  All arguments are CUDA tensors:
-    psi [J, M, N, N] complex64, obj [H, W] complex64, positions [J, 2]
-    int32, probe_in / probe_out [M, N, N] complex64."""
+    details and the size limit).  All arguments are contiguous CUDA tensors
+    on one device: psi [J, M, N, N] complex64, obj [H, W] complex64,
+    positions [J, 2] int32, probe_in / probe_out [M, N, N] complex64.  The
+    call returns once probe_out holds the result."""
     import torch
-    for t in (psi, obj, positions, probe_in, probe_out):
-        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
-            raise ValueError("dm_probe_update_static takes contiguous CUDA tensors")
-    j, m, n, _ = psi.shape
-    h, w = obj.shape
+    j, m, n, h, w = _static_probe_args(psi, obj, positions, probe_in, probe_out)
     if stream is None:
-        stream = torch.cuda.current_stream().cuda_stream
-    rc = load().dm_probe_update_static(psi.data_ptr(), obj.data_ptr(), positions.data_ptr(), probe_in.data_ptr(),
-                                       probe_out.data_ptr(), n, m, j, h, w, float(denom_floor_rel),
-                                       ctypes.c_void_p(int(stream)))
+        stream = torch.cuda.current_stream(psi.device).cuda_stream
+    with torch.cuda.device(psi.device):
+        rc = load().dm_probe_update_static(psi.data_ptr(), obj.data_ptr(), positions.data_ptr(),
+                                           probe_in.data_ptr(), probe_out.data_ptr(), n, m, j, h, w,
+                                           float(denom_floor_rel), ctypes.c_void_p(int(stream)))
     return _check(rc)

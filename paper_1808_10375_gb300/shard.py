@@ -71,8 +71,8 @@ def sharded_iteration(ctxs, allreduce=None):
     for c in ctxs:
         dm.dm_run_step(c, dm.DM_STEP_FOURIER)
     parts = [dm.dm_object_partials(c) for c in ctxs]
-    num = _sum([p[0] for p in parts], np.complex128, allreduce).astype(np.complex64)
-    den = _sum([p[1] for p in parts], np.float64, allreduce).astype(np.float32)
+    num = _sum([p[0] for p in parts], np.complex128, allreduce)
+    den = _sum([p[1] for p in parts], np.float64, allreduce)
     for c in ctxs:
         dm.dm_object_apply(c, num, den)
     parts = [dm.dm_probe_partials(c) for c in ctxs]

@@ -126,3 +126,30 @@ def test_binding_rejects_handles_of_another_kind():
             fn(object())
     with pytest.raises(TypeError):
         dm.dm_free(dm.Net(None, 1))
+
+
+def test_static_probe_update_binding_rejects_bad_tensors():
+    """The binding of dm_probe_update_static checks dtypes, shapes and the
+    device before the C call (a too-small probe_out would be written past its
+    end; int64 positions would be read as wrong pairs)."""
+    import torch
+    from paper_1808_10375_gb300 import dm
+    j, m, n, h, w = 3, 2, 16, 40, 40
+    good = dict(psi=torch.zeros(j, m, n, n, dtype=torch.complex64), obj=torch.zeros(h, w, dtype=torch.complex64),
+                positions=torch.zeros(j, 2, dtype=torch.int32), probe_in=torch.zeros(m, n, n, dtype=torch.complex64),
+                probe_out=torch.zeros(m, n, n, dtype=torch.complex64))
+    bad_cases = [
+        ("positions", torch.zeros(j, 2, dtype=torch.int64), "int32"),
+        ("psi", torch.zeros(j, m, n, n, dtype=torch.complex128), "complex64"),
+        ("probe_out", torch.zeros(m - 1, n, n, dtype=torch.complex64), "probe_out must be"),
+        ("probe_in", torch.zeros(m, n, n + 1, dtype=torch.complex64), "probe_in must be"),
+        ("positions", torch.zeros(j + 1, 2, dtype=torch.int32), "positions must be"),
+        ("obj", torch.zeros(n - 1, w, dtype=torch.complex64), "at least"),
+        ("psi", torch.zeros(j, m, n, n, dtype=torch.complex64).transpose(2, 3), "contiguous"),
+    ]
+    for name, t, msg in bad_cases:
+        args = dict(good, **{name: t})
+        with pytest.raises(ValueError, match=msg):
+            dm._static_probe_args(**args)
+    with pytest.raises(ValueError, match="CUDA"):
+        dm._static_probe_args(**good)

@@ -4,15 +4,19 @@ Some callers of this library cannot allocate device memory: a host
 application that owns all of it and hands the library no allocator, or code
 that must not call cudaMalloc/cudaFree.  dm_probe_update_static gives them the
 probe update (Eq. 4) with its reduction scratch in a fixed array inside the
-library.  This file checks it against the probe update of a normal context
-(dm_run_step with DM_STEP_PROBE) on two calls in a row of different sizes,
-within the parity tolerance of the other GPU tests.  It is collected last and
-passes both alone and after the other tests."""
+library.  This file checks it, on two calls in a row of different sizes,
+against the FP64 oracle's probe update on the same inputs and against the
+probe update of a normal context (dm_run_step with DM_STEP_PROBE), within the
+parity tolerance of the other GPU tests; that the call changes the device's
+free memory by nothing; and that it refuses sizes beyond its array, bad
+positions and a capturing stream.  It is collected last and passes both alone
+and after the other tests."""
 import ctypes
 
 import numpy as np
 import pytest
 
+from oracle import dm as odm
 from parity_util import REL_L2, case, rel_l2
 
 pytestmark = pytest.mark.gpu
@@ -37,30 +41,57 @@ def reference_probe_update(s, p0, o0, psi0, delta_rel):
     return out
 
 
-def static_probe_update(s, p0, o0, psi0, delta_rel):
+def device_args(s, p0, o0, psi0, pos=None):
+    import torch
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    pin = dev(p0)
+    return dict(psi=dev(psi0), obj=dev(o0), pos=dev(s.pos if pos is None else pos), pin=pin,
+                pout=torch.empty_like(pin))
+
+
+def call_static(t, s, delta_rel, stream=None):
     import torch
     from paper_1808_10375_gb300 import dm
     lib = dm.load()
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    psi, obj, pos, pin = dev(psi0), dev(o0), dev(s.pos), dev(p0)
-    pout = torch.empty_like(pin)
     h, w = s.obj_shape
-    stream = torch.cuda.current_stream().cuda_stream
-    rc = lib.dm_probe_update_static(psi.data_ptr(), obj.data_ptr(), pos.data_ptr(), pin.data_ptr(),
-                                    pout.data_ptr(), s.n, s.modes, s.views, h, w, delta_rel,
-                                    ctypes.c_void_p(stream))
-    assert rc == dm.DM_OK, dm.dm_last_error(None)
-    torch.cuda.synchronize()
-    return pout.cpu().numpy()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    return lib.dm_probe_update_static(t["psi"].data_ptr(), t["obj"].data_ptr(), t["pos"].data_ptr(),
+                                      t["pin"].data_ptr(), t["pout"].data_ptr(), s.n, s.modes, s.views, h, w,
+                                      delta_rel, ctypes.c_void_p(stream))
 
 
-def test_static_probe_update_matches_context_update_on_consecutive_calls():
+def test_static_probe_update_matches_oracle_and_context_on_consecutive_calls():
+    import torch
+    from paper_1808_10375_gb300 import dm
     cases = [case(64, 3, (4, 5), 10, (110, 120), 41), case(128, 4, (4, 4), 14, (190, 190), 42)]
     for delta_rel, (s, p0, o0, psi0) in zip((1e-6, 1e-3), cases):
+        want = odm.probe_update(psi0.astype(np.complex128), p0.astype(np.complex128), o0.astype(np.complex128),
+                                s.pos, delta_rel)
         ref = reference_probe_update(s, p0, o0, psi0, delta_rel)
-        got = static_probe_update(s, p0, o0, psi0, delta_rel)
+        t = device_args(s, p0, o0, psi0)
+        torch.cuda.synchronize()
+        rc = call_static(t, s, delta_rel)
+        assert rc == dm.DM_OK, dm.dm_last_error(None)
+        got = t["pout"].cpu().numpy()
         for k in range(s.modes):
+            assert rel_l2(got[k], want[k]) <= REL_L2, (s.n, k, rel_l2(got[k], want[k]))
             assert rel_l2(got[k], ref[k]) <= REL_L2, (s.n, k, rel_l2(got[k], ref[k]))
+
+
+def test_static_probe_update_allocates_no_device_memory():
+    import torch
+    from paper_1808_10375_gb300 import dm
+    s, p0, o0, psi0 = case(64, 2, (3, 3), 10, (90, 90), 44)
+    t = device_args(s, p0, o0, psi0)
+    assert call_static(t, s, 1e-6) == dm.DM_OK, dm.dm_last_error(None)   # warmed up: module loaded
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert call_static(t, s, 1e-6) == dm.DM_OK, dm.dm_last_error(None)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_static_probe_update_rejects_what_does_not_fit():
@@ -76,9 +107,22 @@ def test_static_probe_update_rejects_what_does_not_fit():
     s, p0, o0, psi0 = case(32, 2, (2, 2), 6, (50, 50), 43)
     bad = s.pos.copy()
     bad[1, 0] = 50 - 32 + 1
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    psi, obj, pos, pin = dev(psi0), dev(o0), dev(bad), dev(p0)
-    pout = torch.empty_like(pin)
-    rc = lib.dm_probe_update_static(psi.data_ptr(), obj.data_ptr(), pos.data_ptr(), pin.data_ptr(), pout.data_ptr(),
-                                    32, 2, s.views, 50, 50, 1e-6, None)
+    t = device_args(s, p0, o0, psi0, pos=bad)
+    rc = call_static(t, s, 1e-6, stream=0)
     assert rc == dm.DM_EINVAL and "outside" in dm.dm_last_error(None)
+
+
+def test_static_probe_update_refuses_a_capturing_stream():
+    import torch
+    from paper_1808_10375_gb300 import dm
+    s, p0, o0, psi0 = case(32, 2, (2, 2), 6, (50, 50), 45)
+    t = device_args(s, p0, o0, psi0)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    rcs = []
+    with torch.cuda.graph(g, stream=side):
+        rcs.append(call_static(t, s, 1e-6, stream=side.cuda_stream))
+    assert rcs == [dm.DM_EINVAL] and "captured" in dm.dm_last_error(None)
+    # the stream is usable afterwards and the call works there
+    assert call_static(t, s, 1e-6) == dm.DM_OK, dm.dm_last_error(None)
