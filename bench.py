@@ -57,7 +57,11 @@ def parse():
     ap.add_argument("--views", type=int, default=None, help="use only the first V views (small case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-views", type=int, default=600, help="views in the oracle sample")
+    ap.add_argument("--cpu-views", type=int, default=600, help="views in the one-process oracle sample")
+    ap.add_argument("--cpu-views-per-core", type=int, default=48,
+                    help="views per worker process in the all-cores oracle sample")
+    ap.add_argument("--ref-views-per-core", type=int, default=16,
+                    help="--impl reference: views per worker process in each step's sample")
     ap.add_argument("--tte-iters", type=int, default=3000, help="tte: iteration limit of each DM run")
     ap.add_argument("--tte-train-steps", type=int, default=3000, help="tte: training steps of the warm-start "
                     "network (0: no warm-started run)")
@@ -191,10 +195,24 @@ def stored_traffic(views):
 
 
 def fourier_bytes_per_view(n, m):
-    """Algorithmic bytes of the Fourier-step kernel per view: psi read and
-    write (8 B per complex value per mode each), I read (4 B per pixel) and the
-    object-source write (8 B per pixel)."""
-    return (16 * m + 4 + 8) * n * n
+    """Algorithmic bytes of the Fourier step (exit wave, FFTs, modulus
+    projection, psi update) per view: psi read and write (8 B per complex
+    value per mode each) and I read (4 B per pixel)."""
+    return (16 * m + 4) * n * n
+
+
+def object_source_bytes_per_view(n):
+    """Bytes per view of the object source c_j that the Fourier kernel also
+    writes (8 B per pixel): an intermediate of this implementation, which the
+    object gather reads instead of psi."""
+    return 8 * n * n
+
+
+def fourier_flops_per_view(n, m):
+    """FFT operations of the Fourier step per view, by the usual count of
+    5 L log2(L) real operations per complex transform of L points: two 2-D
+    transforms (forward and inverse) of L = N^2 points per mode."""
+    return 2 * 5 * n * n * int(round(math.log2(n * n))) * m
 
 
 def iteration_bytes_per_view(n, m):
@@ -246,28 +264,89 @@ def oracle_sample(s, p0, o0, views):
     return time.perf_counter() - t0
 
 
+def host_cpu():
+    """(nproc, CPU model) of this host."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_sample_cores(s, p0, o0, views, workers, iters=1):
+    """Oracle iterations over the first `views` views with the views split
+    over `workers` processes (oracle.parallel, as Sec. III splits them over
+    ranks); returns seconds per iteration (the exit waves P O are built
+    before the clock starts)."""
+    from oracle.parallel import ProcessDM
+    import torch
+    inten = s.intensities[:views]
+    inten = inten.cpu().numpy() if isinstance(inten, torch.Tensor) else np.asarray(inten)
+    with ProcessDM(np.ascontiguousarray(inten, np.float32), s.pos[:views], p0.astype(np.complex128),
+                   o0.astype(np.complex128), workers=workers) as pdm:
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            pdm.iterate()
+        return (time.perf_counter() - t0) / iters
+
+
+def cpu_baseline_line(s, p0, o0, j, m, args):
+    """The oracle on the host cores: one process over a view sample and all
+    cores (processes over views) over a larger one, both scaled to
+    view-modes per second."""
+    nproc, model = host_cpu()
+    cv = min(args.cpu_views, j)
+    secs1 = oracle_sample(s, p0, o0, cv)
+    workers = max(1, nproc)
+    cvn = min(j, args.cpu_views_per_core * workers)
+    secsn = oracle_sample_cores(s, p0, o0, cvn, workers)
+    return {"value": cvn * m / secsn, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"one FP64 oracle iteration over the first {cvn} views of the same scan with the views "
+                      f"split over {workers} worker processes (oracle.parallel: Eq. 3 and the Eq. 4/5 partial "
+                      f"sums in the workers, the divisions in the parent): {secsn:.1f} s",
+            "one_core": {"value": cv * m / secs1, "cores": 1,
+                         "sample": f"one FP64 oracle iteration (NumPy, one process) over the first {cv} views: "
+                                   f"{secs1:.1f} s"},
+            "nproc": nproc, "cpu_model": model}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
     import torch
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    views = max(1, args.cpu_views // 6)
+    nproc, model = host_cpu()
+    workers = max(1, nproc)
+    views = max(workers, args.ref_views_per_core * workers)
     s, p0, o0 = make_inputs(views, dev)
     m = s.modes
-    for _ in range(args.warmup):
-        oracle_sample(s, p0, o0, views)
-    tot = 0.0
-    for _ in range(args.steps):
-        tot += oracle_sample(s, p0, o0, views)
+    from oracle.parallel import ProcessDM
+    inten = s.intensities
+    inten = inten.cpu().numpy() if isinstance(inten, torch.Tensor) else np.asarray(inten)
+    with ProcessDM(np.ascontiguousarray(inten, np.float32), s.pos, p0.astype(np.complex128),
+                   o0.astype(np.complex128), workers=workers) as pdm:
+        for _ in range(args.warmup):
+            pdm.iterate()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pdm.iterate()
+        tot = time.perf_counter() - t0
     value = views * m * args.steps / tot
-    sample = f"one FP64 oracle iteration over the first {views} views of {WORKLOAD} per step"
+    sample = (f"one FP64 oracle iteration per step over the first {views} views of {WORKLOAD}, the views split "
+              f"over {workers} worker processes (oracle.parallel); nproc {nproc}, {model}")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "views_per_step": views, "modes": m, "n": s.n,
                    "object": list(s.obj_shape)},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample,
+                         "nproc": nproc, "cpu_model": model},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -739,11 +818,23 @@ def main():
     f_ms, f_n = kt["fourier"]
     hbm, peak_kind = peaks()
     f_bytes = fourier_bytes_per_view(n, m) * j
-    achieved = f_bytes / (f_ms / f_n / 1e3) / 1e9 if f_n else None
+    c_bytes = object_source_bytes_per_view(n) * j
+    launch_s = f_ms / f_n / 1e3 if f_n else None
+    achieved = f_bytes / launch_s / 1e9 if f_n else None
+    fp32_peak = dm.dm_fp32_peak()
+    fft_tflops = fourier_flops_per_view(n, m) * j / launch_s / 1e12 if f_n else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "traffic": stored_traffic(j),
                 "kernel": "k_fourier (persistent Fourier step, Eq. 3)", "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": f_bytes, "avg_launch_ms": f_ms / f_n if f_n else None}
+                "algorithmic_bytes_per_launch": f_bytes, "avg_launch_ms": f_ms / f_n if f_n else None,
+                "object_source_bytes_per_launch": c_bytes,
+                "frac_with_object_source": ((f_bytes + c_bytes) / launch_s / 1e9 / hbm) if f_n else None,
+                "fp32_pipe": {"achieved": fft_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                              "frac": (fft_tflops / fp32_peak) if fft_tflops else None,
+                              "flops_per_launch": fourier_flops_per_view(n, m) * j,
+                              "peak_kind": "measured (dm_fp32_peak, FMA = 2)",
+                              "count": "5 L log2 L per complex transform of L = N^2 points, forward and "
+                                       "inverse, every view and mode"}}
     iter_bytes = iteration_bytes_per_view(n, m) * j
     breakdown = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else None, "launches": v[1],
                      "share": v[0] / max(1e-9, sum(x[0] for x in kt.values()))} for k, v in kt.items()}
@@ -780,11 +871,7 @@ def main():
     # ---- CPU oracle baseline (rank 0, N = 1) ---------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cv = min(args.cpu_views, j)
-        secs = oracle_sample(s, p0, o0, cv)
-        cpu = {"value": cv * m / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one FP64 oracle iteration (NumPy, single thread) over the first {cv} views "
-                         f"of the same scan: {secs:.1f} s"}
+        cpu = cpu_baseline_line(s, p0, o0, j, m, args)
 
     if rank == 0:
         line = {

@@ -190,6 +190,15 @@ int dm_get_psi_error(dm_ctx* ctx, int32_t iter, double* eps_psi);
  * device time of the test kernel (about 2000 ms).  Synchronises. */
 int dm_selftest_bounded_waits(double* elapsed_ms);
 
+/* FP32-pipe peak of the current device in TFLOP/s (a fused multiply-add
+ * counted as two operations), measured by a kernel of eight independent FMA
+ * chains per thread on four 512-thread CTAs per SM, timed with CUDA events
+ * after a warm-up launch: the denominator of the arithmetic roofline of the
+ * Fourier step's FP32 FFTs.  The paper has no counterpart; it is a
+ * measurement utility.  Allocates 4 bytes of device memory, synchronises the
+ * device.  Errors: DM_EINVAL (NULL), DM_ECUDA (message in dm_last_error(NULL)). */
+int dm_fp32_peak(double* tflops);
+
 /* Number of completed dm_iterate iterations. */
 int64_t dm_iterations_done(const dm_ctx* ctx);
 

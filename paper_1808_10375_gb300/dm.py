@@ -59,7 +59,7 @@ EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_
            "dm_object_partials", "dm_object_apply", "dm_probe_partials", "dm_probe_apply",
            "dm_fourier_error_partials", "dm_finish_iteration", "dm_set_graph", "dm_autotune",
            "dm_get_plan", "dm_batch_create", "dm_batch_iterate", "dm_batch_set_graph", "dm_batch_free",
-           "dm_batch_last_error", "dm_dft2", "dm_net_create", "dm_net_param_count", "dm_net_get_params",
+           "dm_batch_last_error", "dm_dft2", "dm_fp32_peak", "dm_net_create", "dm_net_param_count", "dm_net_get_params",
            "dm_net_set_params", "dm_net_forward", "dm_net_gradients", "dm_net_train_step", "dm_net_free"]
 
 _lib = None
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
         "dm_get_error": (ctypes.c_int, [vp, i32, dp, dp, dp]),
         "dm_set_psi_error": (ctypes.c_int, [vp, i32]),
         "dm_selftest_bounded_waits": (ctypes.c_int, [dp]),
+        "dm_fp32_peak": (ctypes.c_int, [dp]),
         "dm_get_psi_error": (ctypes.c_int, [vp, i32, dp]),
         "dm_iterations_done": (i64, [vp]),
         "dm_get_mode_power": (ctypes.c_int, [vp, dp]),
@@ -584,6 +585,15 @@ def dm_get_psi_error(ctx: Context, iteration: int = -1) -> float:
     out = ctypes.c_double()
     _check(load().dm_get_psi_error(ctx.handle, int(iteration), ctypes.byref(out)), ctx)
     return out.value
+
+
+def dm_fp32_peak() -> float:
+    """FP32-pipe peak of the current device in TFLOP/s (see dm.h)."""
+    v = ctypes.c_double()
+    rc = load().dm_fp32_peak(ctypes.byref(v))
+    if rc != DM_OK:
+        raise DMError(rc, (load().dm_last_error(None) or b"").decode())
+    return v.value
 
 
 def dm_selftest_bounded_waits() -> float:

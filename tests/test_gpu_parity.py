@@ -27,7 +27,10 @@ CASES = {
     "n32_m3": (32, 3, (5, 5), 5, (60, 64), 12),
     "n64_m1": (64, 1, (6, 7), 8, (120, 130), 13),
     "n128_m4": (128, 4, (5, 6), 12, (200, 210), 14),
+    # 256 x 256 frames: 8 modes fill the column task's slots, 5 and 7 leave some idle
     "n256_m8": (256, 8, (3, 3), 18, (320, 330), 15),
+    "n256_m5": (256, 5, (3, 2), 20, (310, 300), 19),
+    "n256_m7": (256, 7, (2, 2), 24, (290, 290), 20),
     "n256_m3": (256, 3, (2, 3), 30, (300, 330), 16),
     # fewer modes than column slots: several strips transformed together
     "n256_m1": (256, 1, (2, 2), 40, (300, 300), 17),
