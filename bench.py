@@ -57,12 +57,16 @@ def parse():
     ap.add_argument("--views", type=int, default=None, help="use only the first V views (small case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--psi", choices=["fp32", "fp16"], default="fp32",
+                    help="exit-wave storage of the timed iteration (fp16: the mixed-precision form, no switch)")
     ap.add_argument("--cpu-views", type=int, default=600, help="views in the one-process oracle sample")
     ap.add_argument("--cpu-views-per-core", type=int, default=48,
                     help="views per worker process in the all-cores oracle sample")
     ap.add_argument("--ref-views-per-core", type=int, default=16,
                     help="--impl reference: views per worker process in each step's sample")
     ap.add_argument("--tte-iters", type=int, default=3000, help="tte: iteration limit of each DM run")
+    ap.add_argument("--tte-psi-switch", type=float, default=5e-5,
+                    help="tte: Eq. 6 object change below which the mixed form returns to complex64 exit waves")
     ap.add_argument("--tte-train-steps", type=int, default=3000, help="tte: training steps of the warm-start "
                     "network (0: no warm-started run)")
     ap.add_argument("--workload", choices=["mm256", "batch16", "dft256", "warmstart", "embed", "tte"],
@@ -194,11 +198,12 @@ def stored_traffic(views):
     return d["dram_bytes_per_launch"] * views / d["views"]
 
 
-def fourier_bytes_per_view(n, m):
+def fourier_bytes_per_view(n, m, psi_bytes=8):
     """Algorithmic bytes of the Fourier step (exit wave, FFTs, modulus
-    projection, psi update) per view: psi read and write (8 B per complex
-    value per mode each) and I read (4 B per pixel)."""
-    return (16 * m + 4) * n * n
+    projection, psi update) per view: psi read and write (psi_bytes per
+    complex value per mode each: 8 for complex64, 4 for the complex-half
+    storage of the mixed-precision form) and I read (4 B per pixel)."""
+    return (2 * psi_bytes * m + 4) * n * n
 
 
 def object_source_bytes_per_view(n):
@@ -215,10 +220,10 @@ def fourier_flops_per_view(n, m):
     return 2 * 5 * n * n * int(round(math.log2(n * n))) * m
 
 
-def iteration_bytes_per_view(n, m):
+def iteration_bytes_per_view(n, m, psi_bytes=8):
     """Algorithmic bytes of one DM iteration per view: psi read and written by
     the Fourier step, read by the object and by the probe update, I read."""
-    return (32 * m + 4) * n * n
+    return (4 * psi_bytes * m + 4) * n * n
 
 
 def rank_collectives(pg, device):
@@ -639,20 +644,25 @@ def run_embed(args, rank, local):
 
 
 def run_tte(args, rank, local):
-    """Time to object error 1e-3 of plain FP32 DM on the 4-mode 128x128 scan
-    (2,500 views at 10 px, 640x640 object), simulated without noise so that
-    the reference is the true object.
+    """Time to object error 1e-3 on the 4-mode 128x128 scan (2,500 views at
+    10 px, 640x640 object), simulated without noise so that the reference is
+    the true object: plain FP32 DM against the mixed-precision form
+    (complex-half exit waves, back to complex64 once the Eq. 6 object change
+    drops below --tte-psi-switch).
 
     Error: relative L2 of the object after the best complex scalar, on the
     pixels where sum_j sum_k |P_k|^2 reaches 0.1 of its maximum.  The probe
     is the true one and stays fixed: with the probe free, a linear phase ramp
     moved from the object to the probe changes no intensity, so the object
-    would be fixed only up to that ramp.  Starts: the flat object, a random
-    object (white amplitude in [0.5, 1] and phase in [-pi/2, pi/2], seeded),
-    and the learned start (the network trained here, stitched, with DM's
-    Fourier error after 10 trial iterations choosing between it and the flat
-    start).  Device seconds are CUDA-event time of the iterations alone; the
-    object is copied back and scored every 10 iterations outside it."""
+    would be fixed only up to that ramp.  Starts: a random object (white
+    amplitude in [0.5, 1] and phase in [-pi/2, pi/2], seeded), the flat
+    object, and the judged warm start (the network trained here, stitched,
+    with DM's Fourier error after 10 trial iterations choosing between it and
+    the flat start).  Runs: FP32 from each start, the mixed form from the
+    random and the judged start.  Device seconds are CUDA-event time of the
+    iterations (for the mixed form including its per-iteration check of the
+    switch); the object is copied back and scored every 10 iterations
+    outside it."""
     import torch
     torch.cuda.set_device(local)
     import __graft_entry__
@@ -673,6 +683,7 @@ def run_tte(args, rank, local):
               "random": ((0.5 + 0.5 * rng.random((h, w))) *
                          np.exp(1j * np.pi * (rng.random((h, w)) - 0.5))).astype(np.complex64)}
     train_info = None
+    starts["judged"] = starts["flat"]
     if args.tte_train_steps > 0:
         net = dm.dm_net_create(max_batch=64, seed=11)
         t0 = time.perf_counter()
@@ -684,7 +695,7 @@ def run_tte(args, rank, local):
         chosen, pick, ef = warmstart.judged_start(scan, scan.probe, o_warm, trial_iters=10)
         t_pick = time.perf_counter() - t0
         dm.dm_net_free(net)
-        starts["learned"] = chosen
+        starts["judged"] = chosen
         train_info = {"steps": args.tte_train_steps, "train_s": t_train, "predict_and_judge_s": t_pick,
                       "judge_pick": pick, "fourier_error_after_trial": ef,
                       "predicted_start_error": ws.object_error(o_warm.detach().cpu().numpy(), scan.obj, covered)}
@@ -692,11 +703,16 @@ def run_tte(args, rank, local):
     torch.cuda.set_stream(stream)
     levels = (1e-1, 1e-2, 1e-3)
     block = 10
+    arms = [("fp32_random", "random", dm.DM_PSI_FP32), ("fp32_flat", "flat", dm.DM_PSI_FP32),
+            ("fp32_judged", "judged", dm.DM_PSI_FP32), ("mixed_random", "random", dm.DM_PSI_FP16),
+            ("mixed_judged", "judged", dm.DM_PSI_FP16)]
     runs = {}
     with ClockSampler(gpu_index(local)) as clk:
-        for name, o0 in starts.items():
+        for name, start, prec in arms:
+            o0 = starts[start]
             params = dm.dm_params_default(n=n, modes=m, views=j, obj_h=h, obj_w=w, beta=0.8,
-                                          probe_update_start=1 << 30)
+                                          probe_update_start=1 << 30, psi_precision=prec,
+                                          psi_switch=args.tte_psi_switch if prec == dm.DM_PSI_FP16 else 0.0)
             ctx = dm.dm_init(params, scan.pos, scan.intensities, scan.probe.astype(np.complex64), o0,
                              stream=stream.cuda_stream)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -718,10 +734,13 @@ def run_tte(args, rank, local):
                         first[str(lv)] = {"iterations": it, "device_s": dev_s, "wall_s": time.perf_counter() - t0}
                 if err <= levels[-1]:
                     break
+            prec_now, switched_at = dm.dm_get_psi_precision(ctx)
             dm.dm_free(ctx)
-            runs[name] = {"start_error": start_err, "final_error": err, "iterations": it, "device_s": dev_s,
-                          "ms_per_iteration": 1e3 * dev_s / max(it, 1), "to": first}
-    # the FP64 oracle per iteration on the first 100 views of the same scan, scaled to all views
+            runs[name] = {"start": start, "exit_waves": "complex half, then complex64" if prec else "complex64",
+                          "start_error": start_err, "final_error": err, "iterations": it, "device_s": dev_s,
+                          "ms_per_iteration": 1e3 * dev_s / max(it, 1), "to": first,
+                          "switched_to_complex64_at": switched_at if prec else None}
+    # the FP64 oracle per iteration: one process and all host cores, scaled to all views
     from oracle import dm as odm
     cv = 100
     psi = odm.init_exit_waves(scan.probe.astype(np.complex128), starts["flat"].astype(np.complex128), scan.pos[:cv])
@@ -729,18 +748,32 @@ def run_tte(args, rank, local):
     odm.dm_iteration(psi, scan.probe.astype(np.complex128), starts["flat"].astype(np.complex128), scan.pos[:cv],
                      scan.intensities[:cv].astype(np.float64), update_probe=False)
     cpu_iter_s = (time.perf_counter() - t0) * j / cv
-    base = runs["random"]["to"].get(str(levels[-1]))
+    nproc, model = host_cpu()
+    from oracle.parallel import ProcessDM
+    cvn = min(j, 16 * nproc)
+    with ProcessDM(np.ascontiguousarray(scan.intensities[:cvn], np.float32), scan.pos[:cvn],
+                   scan.probe.astype(np.complex128), starts["flat"].astype(np.complex128), workers=nproc) as pdm:
+        t0 = time.perf_counter()
+        pdm.iterate()
+        cpu_iter_all = (time.perf_counter() - t0) * j / cvn
+    base = runs["fp32_random"]["to"].get(str(levels[-1]))
+    best = runs["mixed_judged"]["to"].get(str(levels[-1]))
     if rank == 0:
         print(json.dumps({
-            "metric": "time to object error 1e-3, plain FP32 DM", "unit": "s",
-            "value": base["device_s"] if base else None, "higher_is_better": False, "n_gpus": 1,
-            "dtype": "f32", "data": "synthetic",
+            "metric": "time to object error 1e-3: warm-started mixed-precision form vs plain FP32 DM from a random start",
+            "unit": "s", "value": best["device_s"] if best else None, "higher_is_better": False, "n_gpus": 1,
+            "fp32_random_s": base["device_s"] if base else None,
+            "speedup_vs_fp32_random": (base["device_s"] / best["device_s"]) if base and best else None,
+            "dtype": "f32 arithmetic; mixed form: exit waves stored as f16 until the switch",
+            "data": "synthetic", "psi_switch": args.tte_psi_switch,
             "config": {"workload": "tte: 4-mode difference map, 128x128 frames, 50x50 scan (2,500 views) at 10 px, "
                                    "640x640 object, noise-free, true probe held fixed, beta 0.8",
                        "error": "relative L2 after the best complex scalar on pixels with sum |P|^2 >= 0.1 max"},
             "runs": runs, "learned": train_info, "clocks": clk.summary(),
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "s_per_iteration": cpu_iter_s,
-                             "sample": f"one FP64 oracle iteration over the first {cv} views, scaled to {j}"},
+            "cpu_baseline": {"kind": "oracle", "cores": nproc, "s_per_iteration": cpu_iter_all,
+                             "sample": f"one FP64 oracle iteration over the first {cvn} views with the views split "
+                                       f"over {nproc} processes, scaled to {j}",
+                             "one_core_s_per_iteration": cpu_iter_s, "cpu_model": model},
         }), flush=True)
 
 
@@ -787,7 +820,8 @@ def main():
     s, p0, o0 = make_inputs(args.views, "cuda")
     n, m, j = s.n, s.modes, s.views
     h, w = s.obj_shape
-    params = dm.dm_params_default(n=n, modes=m, views=j, obj_h=h, obj_w=w, beta=0.8)
+    params = dm.dm_params_default(n=n, modes=m, views=j, obj_h=h, obj_w=w, beta=0.8,
+                                  psi_precision=dm.DM_PSI_FP16 if args.psi == "fp16" else dm.DM_PSI_FP32)
     torch.cuda.synchronize()
     stream = torch.cuda.Stream()          # the library's stream: every kernel and event below
     torch.cuda.set_stream(stream)
@@ -817,7 +851,8 @@ def main():
 
     f_ms, f_n = kt["fourier"]
     hbm, peak_kind = peaks()
-    f_bytes = fourier_bytes_per_view(n, m) * j
+    psi_bytes = 4 if args.psi == "fp16" else 8
+    f_bytes = fourier_bytes_per_view(n, m, psi_bytes) * j
     c_bytes = object_source_bytes_per_view(n) * j
     launch_s = f_ms / f_n / 1e3 if f_n else None
     achieved = f_bytes / launch_s / 1e9 if f_n else None
@@ -835,7 +870,7 @@ def main():
                               "peak_kind": "measured (dm_fp32_peak, FMA = 2)",
                               "count": "5 L log2 L per complex transform of L = N^2 points, forward and "
                                        "inverse, every view and mode"}}
-    iter_bytes = iteration_bytes_per_view(n, m) * j
+    iter_bytes = iteration_bytes_per_view(n, m, psi_bytes) * j
     breakdown = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else None, "launches": v[1],
                      "share": v[0] / max(1e-9, sum(x[0] for x in kt.values()))} for k, v in kt.items()}
 
@@ -877,7 +912,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.psi == "fp32" else "f32 arithmetic, exit waves stored as f16", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC if args.views is None else f"{WORKLOAD_DESC} (first {j} views)",
                        "n": n, "modes": m, "views": j, "object": [h, w], "beta": 0.8,
                        "parallelism": "replicas" if world > 1 else "single GPU",

@@ -108,7 +108,30 @@ typedef struct dm_params {
   int64_t scratch_bytes;      /* L2-resident Fourier-step scratch; 0 = 96 MiB.   */
                               /* Smaller values mean smaller view chunks.        */
   int32_t update_order;       /* DM_ORDER_GAUSS_SEIDEL (default) or DM_ORDER_JACOBI */
+  int32_t psi_precision;      /* exit-wave storage: DM_PSI_FP32 (default) or      */
+                              /* DM_PSI_FP16 (mixed-precision form, n = 64..256)  */
+  double psi_switch;          /* DM_PSI_FP16 only: after the first iteration whose */
+                              /* Eq. 6 object change is below this, the exit waves */
+                              /* become complex64 (0 = never; see below)          */
 } dm_params;
+
+/* Exit-wave storage.  DM_PSI_FP32: complex64.  DM_PSI_FP16, the mixed-
+ * precision form: the exit waves psi are stored as complex half (IEEE
+ * binary16 real and imaginary parts, rounded to nearest even on every store)
+ * and every operation on them is FP32, as in the FP32 form; the probe, the
+ * object, the intensities, the Fourier scratch and all sums keep their
+ * precision.  This halves the bytes of the three exit-wave passes of an
+ * iteration (Fourier-step read and write, probe-update read).  Rounding psi
+ * to 11 significant bits each iteration leaves an error floor near 1e-3
+ * (relative, object), so with psi_switch > 0 dm_iterate returns to complex64
+ * storage once the object's Eq. 6 change drops below psi_switch, and the
+ * iteration is then the FP32 form.  The half form reads that monitor after
+ * every iteration (one device-to-host copy and synchronisation each).  The
+ * paper lists single precision as future work (Sec. V); this form goes one
+ * step further for the stored exit waves only.  Not available with
+ * dm_set_psi_error or in a dm_batch. */
+#define DM_PSI_FP32 0
+#define DM_PSI_FP16 1
 
 /* Order of the overlap projection (Eqs. 4 and 5, written in the paper as
  * simultaneous updates).  Gauss-Seidel: the object from the probe the Fourier
@@ -122,8 +145,8 @@ typedef struct dm_params {
 
 /* Fill p with the defaults: beta 0.8, n_inner 1, probe_update_start 0,
  * denom_floor_rel 1e-6, mem_kind DM_HOST, no allocator, NULL stream,
- * default scratch, Gauss-Seidel order; the sizes are zeroed and must be set
- * by the caller. */
+ * default scratch, Gauss-Seidel order, complex64 exit waves; the sizes are
+ * zeroed and must be set by the caller. */
 void dm_params_default(dm_params* p);
 
 /* Create a context on the current CUDA device: validate the parameters,
@@ -198,6 +221,16 @@ int dm_selftest_bounded_waits(double* elapsed_ms);
  * measurement utility.  Allocates 4 bytes of device memory, synchronises the
  * device.  Errors: DM_EINVAL (NULL), DM_ECUDA (message in dm_last_error(NULL)). */
 int dm_fp32_peak(double* tflops);
+
+/* Switch the exit-wave storage of a context (DM_PSI_FP32 or DM_PSI_FP16):
+ * the exit waves are converted in place (rounded to complex half, or widened
+ * exactly to complex64); captured graphs are dropped.  Synchronises.
+ * dm_get_psi_precision reports the current storage and the iteration count
+ * at which dm_iterate's automatic switch (psi_switch) returned to complex64
+ * (-1 if it has not).  Errors: DM_EINVAL (unknown precision, n without a
+ * half form, exit-wave change tracking on). */
+int dm_set_psi_precision(dm_ctx* ctx, int32_t precision);
+int dm_get_psi_precision(const dm_ctx* ctx, int32_t* precision, int64_t* switched_at);
 
 /* Number of completed dm_iterate iterations. */
 int64_t dm_iterations_done(const dm_ctx* ctx);

@@ -31,9 +31,16 @@ def _attach(spec):
     return shm, np.ndarray(shape, dtype=dtype, buffer=shm.buf)
 
 
-def _worker(conn, a, b, specs, beta, keep):
+def _half(x):
+    """Round complex values to complex half (IEEE binary16 parts, nearest even)."""
+    return x.real.astype(np.float16).astype(np.float64) + 1j * x.imag.astype(np.float16).astype(np.float64)
+
+
+def _worker(conn, a, b, specs, beta, keep, round_start):
     """Holds psi of views [a, b) (or, with keep=False, recomputes it from the
-    initial P O when it is needed again); answers the parent's requests."""
+    initial P O when it is needed again); answers the parent's requests.
+    With round_start the initial exit waves are rounded to complex half (the
+    start of the mixed-precision form)."""
     from oracle import dm as odm
     handles = [_attach(s) for s in specs]
     inten, pos, probe, obj = (h[1] for h in handles)
@@ -41,8 +48,12 @@ def _worker(conn, a, b, specs, beta, keep):
     psi = None
     start = None      # (probe, object) the single Fourier step started from (keep=False)
 
+    def psi0_of(pr, ob, j):
+        p0 = odm.field_products(pr, ob, pos[j])
+        return _half(p0) if round_start else p0
+
     def psi_new_of(i, j):
-        psi0 = odm.field_products(start[0], start[1], pos[j])
+        psi0 = psi0_of(start[0], start[1], j)
         return odm.fourier_update_view(psi0, start[0], start[1], pos[j], inten[j].astype(np.float64), beta)[0]
 
     try:
@@ -51,7 +62,7 @@ def _worker(conn, a, b, specs, beta, keep):
             op = msg[0]
             if op == "init":          # psi = P O on every footprint (Sec. II)
                 if keep:
-                    psi = np.stack([odm.field_products(probe, obj, pos[j]) for j in range(a, b)])
+                    psi = np.stack([psi0_of(probe, obj, j) for j in range(a, b)])
                 conn.send(None)
             elif op == "fourier":     # Eq. 3 on own views, Eq. 5 numerator band
                 if not keep:
@@ -64,7 +75,7 @@ def _worker(conn, a, b, specs, beta, keep):
                 pc = np.conj(probe)
                 ef = isum = d2 = n2 = 0.0
                 for i, j in enumerate(range(a, b)):
-                    old = psi[i] if keep else odm.field_products(probe, obj, pos[j])
+                    old = psi[i] if keep else psi0_of(probe, obj, j)
                     new, e, s = odm.fourier_update_view(old, probe, obj, pos[j], inten[j].astype(np.float64), beta)
                     d2 += float(np.sum(np.abs(new - old) ** 2))
                     n2 += float(np.sum(np.abs(new) ** 2))
@@ -99,9 +110,12 @@ class ProcessDM:
     the initial estimates; ``probe``/``obj`` hold the current estimates
     (FP64).  With ``keep_psi=False`` the workers store no exit waves and
     recompute the new ones for Eq. 4 (one iteration only, for scans whose
-    FP64 exit waves do not fit in host memory).  Use as a context manager."""
+    FP64 exit waves do not fit in host memory).  With ``round_start`` the
+    initial exit waves are rounded to complex half, as the mixed-precision
+    form stores them.  Use as a context manager."""
 
-    def __init__(self, intensities, pos, probe, obj, workers=None, beta=0.8, delta_rel=1e-6, keep_psi=True):
+    def __init__(self, intensities, pos, probe, obj, workers=None, beta=0.8, delta_rel=1e-6, keep_psi=True,
+                 round_start=False):
         self.jn = int(np.asarray(pos).shape[0])
         self.n = probe.shape[-1]
         self.delta_rel = delta_rel
@@ -126,7 +140,7 @@ class ProcessDM:
         try:
             for a, b in zip(bounds[:-1], bounds[1:]):
                 parent, child = ctx.Pipe()
-                p = ctx.Process(target=_worker, args=(child, int(a), int(b), specs, beta, keep_psi), daemon=True)
+                p = ctx.Process(target=_worker, args=(child, int(a), int(b), specs, beta, keep_psi, round_start), daemon=True)
                 p.start()
                 self._procs.append(p)
                 self._conns.append(parent)

@@ -53,7 +53,9 @@ struct dm_ctx {
 
   int N = 0, M = 0, J = 0, H = 0, W = 0;
 
-  float2* psi = nullptr;
+  float2* psi = nullptr;         // exit waves, complex64 (also the staging buffer of the half form)
+  void* psi16 = nullptr;         // exit waves as complex half (mixed-precision form), or null
+  bool half = false;             // the exit waves currently live in psi16
   float2* probe[2] = {nullptr, nullptr};
   float2* obj[2] = {nullptr, nullptr};
   float2* cview = nullptr;
@@ -102,6 +104,7 @@ struct dm_ctx {
   int probe_groups = 0;
   int probe_final_blocks = 0;
   int64_t iters = 0;
+  int64_t switched_at = -1;      // iteration count when the exit waves went back to complex64
   bool use_graph = false;
   cudaStream_t cap_stream = nullptr;   // private stream the iteration graphs are captured on
   cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // by (cur_O, cur_P)
@@ -157,6 +160,10 @@ void dev_free(dm_ctx* c, void* ptr) {
   c->bytes -= it->second;
   c->allocs.erase(it);
 }
+
+// The exit waves in their current storage form.
+void* psi_cur(const dm_ctx* c) { return c->half ? c->psi16 : static_cast<void*>(c->psi); }
+size_t psi_elem_bytes(const dm_ctx* c) { return c->half ? 4 : sizeof(float2); }
 
 template <typename T>
 int alloc_n(dm_ctx* c, T** out, size_t n) {
@@ -367,7 +374,8 @@ int plan_fourier(dm_ctx* c, const FourierKnobs& k) {
                              c->stream));
   DM_CUDA(c, cudaStreamSynchronize(c->stream));  // `off` is a host temporary
   if ((rc = encode_scratch_map(c, a, c->scratch, c->tmap_s))) return rc;
-  a.psi = c->psi; a.istrip = c->istrip; a.pos = c->pos; a.cview = c->cview;
+  a.psi = psi_cur(c); a.psi16 = c->half ? 1 : 0;
+  a.istrip = c->istrip; a.pos = c->pos; a.cview = c->cview;
   a.scratch = c->scratch; a.ef_part = c->ef_part; a.tw = c->tw;
   a.stage_off = c->stage_off; a.counters = c->counters; a.status = c->status;
   a.psi_part = c->psi_err ? c->psi_part : nullptr;
@@ -452,6 +460,8 @@ int run_fourier(dm_ctx* c) {
   DM_CUDA(c, cudaMemsetAsync(c->counters, 0, c->counters_bytes, c->stream));
   c->fa.probe = c->probe[c->cur_P];
   c->fa.obj = c->obj[c->cur_O];
+  c->fa.psi = psi_cur(c);
+  c->fa.psi16 = c->half ? 1 : 0;
   Timed t(c, DM_KERNEL_FOURIER);
   DM_CUDA(c, dmk::launch_fourier(c->tmap_s, c->fa, c->fgrid, c->fsmem, c->stream));
   return DM_OK;
@@ -502,7 +512,8 @@ dmk::ProbeFinalArgs probe_final_args(dm_ctx* c) {
 int run_probe_sums(dm_ctx* c, const float2* o) {
   dmk::ProbePartialArgs a{};
   a.N = c->N; a.M = c->M; a.J = c->J; a.H = c->H; a.W = c->W; a.groups = c->probe_groups;
-  a.psi = c->psi; a.obj = o; a.pos = c->pos; a.part_num = c->part_num; a.part_den = c->part_den;
+  a.psi = psi_cur(c); a.psi16 = c->half ? 1 : 0;
+  a.obj = o; a.pos = c->pos; a.part_num = c->part_num; a.part_den = c->part_den;
   a.status = c->status;
   {
     Timed t(c, DM_KERNEL_PROBE_PARTIAL);
@@ -564,6 +575,8 @@ void dm_params_default(dm_params* p) {
   p->probe_update_start = 0;
   p->denom_floor_rel = 1e-6;
   p->mem_kind = DM_HOST;
+  p->psi_precision = DM_PSI_FP32;
+  p->psi_switch = 0.0;
 }
 
 int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const float* intensities,
@@ -591,6 +604,12 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
     return fail(nullptr, DM_EINVAL, "unknown update_order");
   if (p->update_order == DM_ORDER_JACOBI && p->n_inner != 1)
     return fail(nullptr, DM_EINVAL, "the Jacobi order takes n_inner = 1");
+  if (p->psi_precision != DM_PSI_FP32 && p->psi_precision != DM_PSI_FP16)
+    return fail(nullptr, DM_EINVAL, "unknown psi_precision");
+  if (p->psi_precision == DM_PSI_FP16 && !dmk::fourier_has_psi16(p->n))
+    return fail(nullptr, DM_EINVAL, "complex-half exit waves need n = 64, 128 or 256");
+  if (!(p->psi_switch >= 0.0) || !std::isfinite(p->psi_switch))
+    return fail(nullptr, DM_EINVAL, "psi_switch must be finite and >= 0");
   if (p->mem_kind == DM_HOST) {
     for (int j = 0; j < p->views; ++j) {
       const int r = positions[2 * j], q = positions[2 * j + 1];
@@ -644,6 +663,10 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   int rc;
 #define DM_TRY(x) do { if ((rc = (x)) != DM_OK) return bail(rc); } while (0)
   DM_TRY(alloc_n(c, &c->psi, (size_t)J * M * nn));
+  if (p->psi_precision == DM_PSI_FP16) {
+    DM_TRY(dev_alloc(c, &c->psi16, (size_t)J * M * nn * 4));
+    c->half = true;
+  }
   DM_TRY(alloc_n(c, &c->cview, (size_t)J * nn));
   DM_TRY(alloc_n(c, &c->istrip, (size_t)J * nn));
   DM_TRY(alloc_n(c, &c->probe[0], (size_t)M * nn));
@@ -694,7 +717,8 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
     cuda_fail(c, e, "intensity sum"); return bail(DM_ECUDA);
   }
   if ((e = dmk::launch_p2(c->p2, c->probe[0], N, M, c->stream)) != cudaSuccess) { cuda_fail(c, e, "p2"); return bail(DM_ECUDA); }
-  if ((e = dmk::launch_init_psi(c->psi, c->probe[0], c->obj[0], c->pos, N, M, J, c->W, c->stream)) != cudaSuccess) {
+  if ((e = dmk::launch_init_psi(psi_cur(c), c->half ? 1 : 0, c->probe[0], c->obj[0], c->pos, N, M, J, c->W,
+                                c->stream)) != cudaSuccess) {
     cuda_fail(c, e, "initial exit waves"); return bail(DM_ECUDA);
   }
   DM_TRY(check_status(c));
@@ -731,7 +755,8 @@ int enqueue_iteration(dm_ctx* c, bool upd) {
   for (int pass = 0; pass < c->p.n_inner; ++pass) {
     if (pass > 0) {
       Timed t(c, DM_KERNEL_OTHER);
-      DM_CUDA(c, dmk::launch_obj_source(c->cview, c->psi, c->probe[c->cur_P ^ 1], c->N, c->M, c->J, c->stream));
+      DM_CUDA(c, dmk::launch_obj_source(c->cview, psi_cur(c), c->half ? 1 : 0, c->probe[c->cur_P ^ 1], c->N, c->M, c->J,
+                                             c->stream));
     }
     if ((rc = run_object(c))) return rc;
     if (!upd) break;  // later passes would repeat the same object update
@@ -768,6 +793,29 @@ int iteration_graph(dm_ctx* c, cudaGraphExec_t* out) {
   return DM_OK;
 }
 
+// Switch the exit-wave storage between complex64 and complex half.
+int set_psi_precision(dm_ctx* c, int32_t precision) {
+  const bool want_half = precision == DM_PSI_FP16;
+  if (want_half == c->half) return DM_OK;
+  const size_t n = (size_t)c->J * c->M * c->N * c->N;
+  if (want_half) {
+    if (!dmk::fourier_has_psi16(c->N)) return fail(c, DM_EINVAL, "complex-half exit waves need n = 64, 128 or 256");
+    if (c->psi_err) return fail(c, DM_EINVAL, "the exit-wave change is tracked with complex64 exit waves only");
+    int rc;
+    if (!c->psi16 && (rc = dev_alloc(c, &c->psi16, n * 4))) return rc;
+    DM_CUDA(c, dmk::launch_psi_convert(c->psi16, c->psi, n, 1, c->stream));
+  } else {
+    DM_CUDA(c, dmk::launch_psi_convert(c->psi, c->psi16, n, 0, c->stream));
+  }
+  c->half = want_half;
+  c->switched_at = want_half ? -1 : c->iters;
+  // captured iterations launched the other kernel instances on the other buffer
+  for (auto& row : c->gexec)
+    for (auto& g : row)
+      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  return DM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -788,7 +836,33 @@ int dm_iterate(dm_ctx* c, int32_t n_iter) {
     c->cur_O ^= 1;
     if (upd) c->cur_P ^= 1;
     c->iters++;
+    // mixed-precision form: complex-half exit waves until the object's Eq. 6
+    // change falls below psi_switch, then complex64 for the rest of the run
+    if (c->half && c->p.psi_switch > 0.0) {
+      double eps_obj = 0.0;
+      DM_CUDA(c, cudaMemcpyAsync(&eps_obj, c->ring + (size_t)((c->iters - 1) % dmk::kMetricsRing) * dmk::kRingRow,
+                                 sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      DM_CUDA(c, cudaStreamSynchronize(c->stream));
+      if (eps_obj < c->p.psi_switch && (rc = set_psi_precision(c, DM_PSI_FP32))) return rc;
+    }
   }
+  return DM_OK;
+}
+
+int dm_set_psi_precision(dm_ctx* c, int32_t precision) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (precision != DM_PSI_FP32 && precision != DM_PSI_FP16) return fail(c, DM_EINVAL, "unknown psi precision");
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));   // no captured iteration is in flight
+  if ((rc = set_psi_precision(c, precision))) return rc;
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DM_OK;
+}
+
+int dm_get_psi_precision(const dm_ctx* c, int32_t* precision, int64_t* switched_at) {
+  if (!c || c->magic != 0x58434D44u) return DM_EINVAL;
+  if (precision) *precision = c->half ? DM_PSI_FP16 : DM_PSI_FP32;
+  if (switched_at) *switched_at = c->switched_at;
   return DM_OK;
 }
 
@@ -837,14 +911,16 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
     return rc;
   }
   // the tuning runs change the exit waves of the sample views: keep a copy
-  DM_CUDA(c, cudaMemcpyAsync(psi_save, c->psi, psi_elems * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+  DM_CUDA(c, cudaMemcpyAsync(psi_save, psi_cur(c), psi_elems * psi_elem_bytes(c), cudaMemcpyDeviceToDevice,
+                             c->stream));
   cudaEvent_t e0 = take_event(c), e1 = take_event(c);
   double best = 1e300;
   FourierKnobs best_k = c->knobs;
   constexpr int kReps = 3;
   for (Plan& pl : plans) {
     dmk::FourierArgs a = pl.a;
-    a.psi = c->psi; a.istrip = c->istrip; a.pos = c->pos; a.cview = c->cview; a.scratch = scr; a.ef_part = ef;
+    a.psi = psi_cur(c); a.psi16 = c->half ? 1 : 0;
+    a.istrip = c->istrip; a.pos = c->pos; a.cview = c->cview; a.scratch = scr; a.ef_part = ef;
     a.tw = c->tw; a.stage_off = offd; a.counters = cnt; a.status = c->status;
     a.probe = c->probe[c->cur_P]; a.obj = c->obj[c->cur_O];
     CUtensorMap map[2];
@@ -867,7 +943,8 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
   }
   c->event_pool.push_back(e0);
   c->event_pool.push_back(e1);
-  DM_CUDA(c, cudaMemcpyAsync(c->psi, psi_save, psi_elems * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+  DM_CUDA(c, cudaMemcpyAsync(psi_cur(c), psi_save, psi_elems * psi_elem_bytes(c), cudaMemcpyDeviceToDevice,
+                             c->stream));
   release();
   if ((rc = check_status(c))) return rc;
   // re-plan the whole scan with the fastest knobs (captured graphs hold the
@@ -968,7 +1045,7 @@ int enqueue_batch_iteration(dm_batch* b) {
     int rc = DM_OK;
     for (int pass = 0; pass < c->p.n_inner && rc == DM_OK; ++pass) {
       if (pass > 0) {
-        const cudaError_t e = dmk::launch_obj_source(c->cview, c->psi, c->probe[c->cur_P ^ 1], c->N, c->M, c->J,
+        const cudaError_t e = dmk::launch_obj_source(c->cview, psi_cur(c), c->half ? 1 : 0, c->probe[c->cur_P ^ 1], c->N, c->M, c->J,
                                                      c->stream);
         if (e != cudaSuccess) rc = cuda_fail(c, e, "object source");
       }
@@ -999,6 +1076,7 @@ int dm_batch_create(dm_batch** out, dm_ctx* const* ctxs, int32_t count) {
   for (int i = 0; i < count; ++i) {
     if (!ctxs[i]) { delete b; return batch_fail(nullptr, DM_EINVAL, "a context is NULL"); }
     if (ctxs[i]->device != b->device) { delete b; return batch_fail(nullptr, DM_EINVAL, "contexts on different devices"); }
+    if (ctxs[i]->half) { delete b; return batch_fail(nullptr, DM_EINVAL, "a context stores complex-half exit waves"); }
     for (int k = 0; k < i; ++k)
       if (ctxs[k] == ctxs[i]) { delete b; return batch_fail(nullptr, DM_EINVAL, "a context appears twice"); }
     b->ctx.push_back(ctxs[i]);
@@ -1133,7 +1211,8 @@ int dm_run_step(dm_ctx* c, int32_t step) {
     case DM_STEP_OBJECT: {
       {
         Timed t(c, DM_KERNEL_OTHER);
-        DM_CUDA(c, dmk::launch_obj_source(c->cview, c->psi, c->probe[c->cur_P], c->N, c->M, c->J, c->stream));
+        DM_CUDA(c, dmk::launch_obj_source(c->cview, psi_cur(c), c->half ? 1 : 0, c->probe[c->cur_P], c->N, c->M, c->J,
+                                             c->stream));
       }
       if ((rc = run_object(c))) return rc;
       c->cur_O ^= 1;
@@ -1253,7 +1332,10 @@ int dm_get_exit_waves(dm_ctx* c, float* out, int32_t mem_kind) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!out || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad output");
-  if ((rc = copy_out(c, out, c->psi, (size_t)c->J * c->M * c->N * c->N * sizeof(float2), mem_kind))) return rc;
+  const size_t n = (size_t)c->J * c->M * c->N * c->N;
+  // the half form is widened into the complex64 buffer first (exactly: every half is a float)
+  if (c->half) DM_CUDA(c, dmk::launch_psi_convert(c->psi, c->psi16, n, 0, c->stream));
+  if ((rc = copy_out(c, out, c->psi, n * sizeof(float2), mem_kind))) return rc;
   return check_status(c);
 }
 
@@ -1261,10 +1343,14 @@ int dm_set_exit_waves(dm_ctx* c, const float* in, int32_t mem_kind) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!in || (mem_kind != DM_HOST && mem_kind != DM_DEVICE)) return fail(c, DM_EINVAL, "bad input");
-  if ((rc = copy_in(c, c->psi, in, (size_t)c->J * c->M * c->N * c->N * sizeof(float2), mem_kind))) return rc;
+  const size_t n = (size_t)c->J * c->M * c->N * c->N;
+  if ((rc = copy_in(c, c->psi, in, n * sizeof(float2), mem_kind))) return rc;
+  // the half form keeps the values rounded to complex half
+  if (c->half) DM_CUDA(c, dmk::launch_psi_convert(c->psi16, c->psi, n, 1, c->stream));
   DM_CUDA(c, cudaStreamSynchronize(c->stream));
   return DM_OK;
 }
+
 
 int dm_set_object(dm_ctx* c, const float* in, int32_t mem_kind) {
   int rc = check_ctx(c);
@@ -1306,6 +1392,7 @@ int dm_get_error(dm_ctx* c, int32_t iter, double* eps_obj, double* eps_probe, do
 int dm_set_psi_error(dm_ctx* c, int32_t enable) {
   int rc = check_ctx(c);
   if (rc) return rc;
+  if (enable && c->half) return fail(c, DM_EINVAL, "the exit-wave change is tracked with complex64 exit waves only");
   DM_CUDA(c, cudaStreamSynchronize(c->stream));   // no captured iteration is in flight below
   if (enable && !c->psi_part && (rc = alloc_n(c, &c->psi_part, (size_t)c->J * c->fa.RB * 2))) return rc;
   c->psi_err = enable != 0;

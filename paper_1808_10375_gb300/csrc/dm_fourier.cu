@@ -27,6 +27,7 @@
 
 #include "dm_fft.cuh"
 #include "dm_kernels.h"
+#include "dm_psi.cuh"
 #include "dm_ptx.cuh"
 
 namespace dmk {
@@ -61,7 +62,7 @@ __device__ __forceinline__ float2* row_buf(float2* stage, int g, int i) {
 // it starts at any column); the buffers belong to the group, so only
 // warp-level sync is needed.  psi, the stream from DRAM, is requested a whole
 // mode ahead; P (L2-resident) once the exchange has freed buffer B.
-template <int N>
+template <int N, class PsiT = float2>
 __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* stage, const float2* twF,
                                             int j, int jj, int rb, float2* slot) {
   using C = FCfg<N>;
@@ -75,10 +76,19 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* stage,
   float2* orow_s = row_buf<N>(stage, g, 1);    // O: object row
   float2* xg = prow_s;
   const uint64_t pol_first = l2_policy_evict_first(), pol_last = l2_policy_evict_last();
+  // psi rows are N values of PsiT: N * sizeof(PsiT) / 16 copies of 16 bytes
   auto issue_psi = [&](int k) {
-    const float2* src = a.psi + (((size_t)j * a.M + k) * N + y) * N;
-    for (int q = t; q < N / 2; q += C::R2) cp_async16_hint(srow_s + 2 * q, src + 2 * q, pol_first);
+    if constexpr (sizeof(PsiT) == sizeof(float2)) {
+      const float2* src = static_cast<const float2*>(a.psi) + (((size_t)j * a.M + k) * N + y) * N;
+      for (int q = t; q < N / 2; q += C::R2) cp_async16_hint(srow_s + 2 * q, src + 2 * q, pol_first);
+    } else {
+      constexpr int kPsiChunks = N * (int)sizeof(PsiT) / 16;
+      const char* src = reinterpret_cast<const char*>(static_cast<const PsiT*>(a.psi) + (((size_t)j * a.M + k) * N + y) * N);
+      char* dst = reinterpret_cast<char*>(srow_s);
+      for (int q = t; q < kPsiChunks; q += C::R2) cp_async16_hint(dst + 16 * q, src + 16 * q, pol_first);
+    }
   };
+  const PsiT* srow_t = reinterpret_cast<const PsiT*>(srow_s);
   auto issue_p = [&](int k) {
     const float2* src = a.probe + ((size_t)k * N + y) * N;
     for (int q = t; q < N / 2; q += C::R2) cp_async16_hint(prow_s + 2 * q, src + 2 * q, pol_last);
@@ -95,7 +105,7 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* stage,
     for (int i = 0; i < C::R1; ++i) {
       const int x = t + C::R2 * i;
       const float2 po = cmul(prow_s[x], orow_s[x]);
-      const float2 s = srow_s[x];
+      const float2 s = psi_ld(srow_t + x);
       v[i] = make_float2(fmaf(2.f, po.x, -s.x), fmaf(2.f, po.y, -s.y));
     }
     __syncwarp();
@@ -130,7 +140,7 @@ __device__ __forceinline__ void row_forward(const FourierArgs& a, float2* stage,
 // at k = 0), then P_k.  With PSIERR the old exit waves are read back before
 // they are overwritten, and the thread's sums of |psi' - psi|^2 and |psi'|^2
 // are returned (zero otherwise).
-template <int N, bool PSIERR>
+template <int N, bool PSIERR, class PsiT = float2>
 __device__ __forceinline__ float2 row_inverse(const FourierArgs& a, float2* stage, const float2* twF,
                                               int j, int jj, int rb, const float2* slot) {
   using C = FCfg<N>;
@@ -179,7 +189,7 @@ __device__ __forceinline__ float2 row_inverse(const FourierArgs& a, float2* stag
     fft_pass2<N, true>(v);
     if (more) cp_async_wait<1>(); else cp_async_wait<0>();   // P_k
     __syncwarp();
-    float2* srow = a.psi + (((size_t)j * a.M + k) * N + y) * N;
+    PsiT* srow = static_cast<PsiT*>(a.psi) + (((size_t)j * a.M + k) * N + y) * N;
 #pragma unroll
     for (int d = 0; d < C::D; ++d) {
 #pragma unroll
@@ -190,12 +200,12 @@ __device__ __forceinline__ float2 row_inverse(const FourierArgs& a, float2* stag
         const float2 g2 = v[p2_index<N>(d, k2)];
         const float2 pn = make_float2(fmaf(c2b, po.x, g2.x), fmaf(c2b, po.y, g2.y));
         if constexpr (PSIERR) {
-          const float2 old = __ldcs(srow + x);
+          const float2 old = psi_ldcs(srow + x);
           const float2 dv = csub(pn, old);
           perr.x += cnorm(dv);
           perr.y += cnorm(pn);
         }
-        __stcs(srow + x, pn);
+        psi_stcs(srow + x, pn);
         const float2 cn = cconjmul(pk, pn);
         cacc[d * C::R2 + k2] = k == 0 ? cn : cadd(cacc[d * C::R2 + k2], cn);
       }
@@ -680,7 +690,7 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
 // One scan: the same task loop as fourier_tasks, specialised to one scan
 // whose arguments are the kernel's own parameters (which keeps its register
 // allocation lean); its task counter is counters[0].
-template <int N, bool GANG, bool PSIERR>
+template <int N, bool GANG, bool PSIERR, class PsiT = float2>
 __global__ void __launch_bounds__(kThreads, 2)
     k_fourier(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap1,
               const FourierArgs a) {
@@ -780,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       float2* slot = a.scratch + (size_t)sl * slot_elems;
       if (kind == 0) {
         const int jj = local / a.RB, rb = local % a.RB;
-        row_forward<N>(a, stage, tw, c * a.B + jj, jj, rb, slot);
+        row_forward<N, PsiT>(a, stage, tw, c * a.B + jj, jj, rb, slot);
       } else if (kind == 1) {
         const int jj = local / a.CG, sg = local % a.CG;
         const int j = c * a.B + jj;
@@ -797,7 +807,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
       } else {
         const int jj = local / a.RB, rb = local % a.RB;
-        const float2 pe = row_inverse<N, PSIERR>(a, stage, tw, c * a.B + jj, jj, rb, slot);
+        const float2 pe = row_inverse<N, PSIERR, PsiT>(a, stage, tw, c * a.B + jj, jj, rb, slot);
         if constexpr (PSIERR) {
           // this task's exit-wave change sums, in FP64 across the CTA
           double d2 = pe.x, n2 = pe.y;
@@ -901,7 +911,9 @@ size_t fourier_smem_bytes(int N, int M, int bufs, int G) {
 
 // The single-scan kernel: the gang form for every frame size, and for
 // N = 256 also the one-strip form (the modes fill the slots by themselves);
-// each with and without the exit-wave change sums.
+// each with and without the exit-wave change sums.  The mixed-precision
+// form (exit waves stored as complex half) exists for N = 64, 128 and 256,
+// without the exit-wave change sums.
 template <bool PSIERR>
 static const void* fourier_kernel_t(int N, bool gang) {
   switch (N) {
@@ -914,7 +926,20 @@ static const void* fourier_kernel_t(int N, bool gang) {
   }
 }
 
-static const void* fourier_kernel(int N, bool gang, bool psierr) {
+static const void* fourier_kernel_h(int N, bool gang) {
+  switch (N) {
+    case 64: return (const void*)k_fourier<64, true, false, __half2>;
+    case 128: return (const void*)k_fourier<128, true, false, __half2>;
+    case 256: return gang ? (const void*)k_fourier<256, true, false, __half2>
+                          : (const void*)k_fourier<256, false, false, __half2>;
+    default: return nullptr;
+  }
+}
+
+bool fourier_has_psi16(int N) { return N == 64 || N == 128 || N == 256; }
+
+static const void* fourier_kernel(int N, bool gang, bool psierr, bool psi16) {
+  if (psi16) return psierr ? nullptr : fourier_kernel_h(N, gang);
   return psierr ? fourier_kernel_t<true>(N, gang) : fourier_kernel_t<false>(N, gang);
 }
 
@@ -933,9 +958,10 @@ static cudaError_t allow_max_smem(const void* f) {
 // forms), with every form's shared-memory limit set.
 int fourier_occupancy(int N, size_t smem) {
   int best = -1;
-  for (bool psierr : {false, true})
+  for (int form = 0; form < 3; ++form)   // FP32, FP32 with the exit-wave change, complex-half exit waves
     for (bool gang : {true, false}) {
-      const void* f = fourier_kernel(N, gang, psierr);
+      if (form == 2 && !fourier_has_psi16(N)) continue;
+      const void* f = fourier_kernel(N, gang, form == 1, form == 2);
       if (!f) return 0;
       if (allow_max_smem(f) != cudaSuccess) return 0;
       int nb = 0;
@@ -998,10 +1024,25 @@ static cudaError_t launch_fourier_t(const CUtensorMap& m, const CUtensorMap& m1,
   return cudaGetLastError();
 }
 
+static cudaError_t launch_fourier_h(const CUtensorMap& m, const CUtensorMap& m1, const FourierArgs& a, int grid,
+                                    size_t smem, cudaStream_t s) {
+  switch (a.N) {
+    case 64: k_fourier<64, true, false, __half2><<<grid, kThreads, smem, s>>>(m, m1, a); break;
+    case 128: k_fourier<128, true, false, __half2><<<grid, kThreads, smem, s>>>(m, m1, a); break;
+    case 256:
+      if (a.G > 1) k_fourier<256, true, false, __half2><<<grid, kThreads, smem, s>>>(m, m1, a);
+      else k_fourier<256, false, false, __half2><<<grid, kThreads, smem, s>>>(m, m1, a);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // The instance follows the plan: the gang form when G > 1, the exit-wave
-// change sums when a.psi_part is set.
+// change sums when a.psi_part is set, complex-half exit waves when a.psi16.
 cudaError_t launch_fourier(const void* tmaps, const FourierArgs& a, int grid, size_t smem, cudaStream_t s) {
   const CUtensorMap* m = static_cast<const CUtensorMap*>(tmaps);
+  if (a.psi16) return a.psi_part ? cudaErrorInvalidValue : launch_fourier_h(m[0], m[1], a, grid, smem, s);
   return a.psi_part ? launch_fourier_t<true>(m[0], m[1], a, grid, smem, s)
                     : launch_fourier_t<false>(m[0], m[1], a, grid, smem, s);
 }

@@ -41,7 +41,8 @@ constexpr int kTwBytes = 2048;         // shared twiddle table (N <= 256 complex
 struct FourierArgs {
   int N, M, J, H, W;
   float beta;
-  float2* psi;            // [J][M][N][N]
+  void* psi;              // [J][M][N][N] complex64, or complex half when psi16
+  int psi16;              // 1: the exit waves are stored as complex half (mixed-precision form)
   const float* istrip;    // intensities in strip layout [J][NS][N][w]
   const float2* probe;    // [M][N][N]
   const float2* obj;      // [H][W]
@@ -137,7 +138,8 @@ constexpr int kProbeStages = 3;        // depth of the views' shared-memory ring
 
 struct ProbePartialArgs {
   int N, M, J, H, W, groups;
-  const float2* psi;
+  const void* psi;         // complex64, or complex half when psi16
+  int psi16;
   const float2* obj;
   const int2* pos;
   float2* part_num;        // [groups][M][N*N]
@@ -171,7 +173,7 @@ int fourier_twiddles(int N, float2* tab);
 
 cudaError_t launch_obj_gather(const void* tmap, const ObjGatherArgs& a, int ntiles, cudaStream_t s);
 cudaError_t launch_obj_final(const ObjFinalArgs& a, int blocks, cudaStream_t s);
-cudaError_t launch_obj_source(float2* cview, const float2* psi, const float2* probe, int N, int M,
+cudaError_t launch_obj_source(float2* cview, const void* psi, int psi16, const float2* probe, int N, int M,
                               int J, cudaStream_t s);
 // Pixels per probe tile and the probe-partial kernel's dynamic shared memory.
 int probe_tile_px(int M);
@@ -189,8 +191,13 @@ cudaError_t launch_probe_div(const ProbeFinalArgs& a, cudaStream_t s, int* block
 cudaError_t launch_max_f32(const float* x, size_t n, unsigned* bits, cudaStream_t s);
 cudaError_t launch_max_f64(const double* x, size_t n, unsigned long long* bits, cudaStream_t s);
 
-cudaError_t launch_init_psi(float2* psi, const float2* probe, const float2* obj, const int2* pos,
+cudaError_t launch_init_psi(void* psi, int psi16, const float2* probe, const float2* obj, const int2* pos,
                             int N, int M, int J, int W, cudaStream_t s);
+// Exit waves between the two storage forms (n complex values): to_half = 1
+// rounds complex64 to complex half, 0 widens complex half to complex64.
+cudaError_t launch_psi_convert(void* dst, const void* src, size_t n, int to_half, cudaStream_t s);
+// Whether the Fourier kernel has a complex-half form for N x N frames.
+bool fourier_has_psi16(int N);
 cudaError_t launch_intensity_layout(float* istrip, const float* inten, int N, int J, int w,
                                     double* isum_part, int* status, int* blocks_out, cudaStream_t s);
 cudaError_t launch_p2(float* p2, const float2* probe, int N, int M, cudaStream_t s);

@@ -10,6 +10,7 @@
 
 #include "dm_fft.cuh"
 #include "dm_kernels.h"
+#include "dm_psi.cuh"
 #include "dm_ptx.cuh"
 
 namespace dmk {
@@ -200,14 +201,15 @@ __global__ void __launch_bounds__(kThreads) k_obj_final64(const ObjFinal64Args a
 
 // c_j(u) = sum_k conj(P_k(u)) psi_j^k(u): the object source, recomputed from
 // the exit waves when an inner overlap pass has changed the probe.
-__global__ void __launch_bounds__(kThreads) k_obj_source(float2* cview, const float2* psi,
+template <class PsiT>
+__global__ void __launch_bounds__(kThreads) k_obj_source(float2* cview, const PsiT* psi,
                                                          const float2* probe, int N, int M, int J) {
   const size_t nn = (size_t)N * N;
   const size_t tot = (size_t)J * nn;
   for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < tot; i += (size_t)gridDim.x * kThreads) {
     const size_t j = i / nn, u = i % nn;
     float2 acc = make_float2(0.f, 0.f);
-    for (int k = 0; k < M; ++k) acc = cadd(acc, cconjmul(__ldg(probe + k * nn + u), __ldcs(psi + (j * M + k) * nn + u)));
+    for (int k = 0; k < M; ++k) acc = cadd(acc, cconjmul(__ldg(probe + k * nn + u), psi_ldcs(psi + (j * M + k) * nn + u)));
     cview[i] = acc;
   }
 }
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(kThreads) k_obj_source(float2* cview, const fl
 // the object values of its own pixels with 8-byte asynchronous copies, so
 // several views' reads are in flight while one is summed.
 // ---------------------------------------------------------------------------
-template <int MAXM, int PX>
+template <int MAXM, int PX, class PsiT>
 __global__ void __launch_bounds__(kThreads, 2) k_probe_partial(const ProbePartialArgs a) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kProbeStages];
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_probe_partial(const ProbePartia
     const int nv = j1 - j0;
     const int u0 = tile * TP;
     const int npx = min(TP, nn - u0);               // a multiple of 256 (nn is)
-    const uint32_t mode_bytes = (uint32_t)npx * sizeof(float2);
+    const uint32_t mode_bytes = (uint32_t)npx * sizeof(PsiT);   // a mode's tile of psi (its slot holds float2)
     int uy[PX], ux[PX];
     bool ok[PX];
     float2 acc[PX][MAXM];
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_probe_partial(const ProbePartia
       if (threadIdx.x == 0) {
         uint64_t* bar = &full[issued % kProbeStages];
         mbar_arrive_expect_tx(bar, mode_bytes * (uint32_t)M);
-        const float2* src = a.psi + (size_t)(j0 + i) * M * nn + u0;
+        const PsiT* src = static_cast<const PsiT*>(a.psi) + (size_t)(j0 + i) * M * nn + u0;
         for (int k = 0; k < M; ++k) bulk_load(st + k * TP, src + (size_t)k * nn, mode_bytes, bar);
       }
 #pragma unroll
@@ -304,7 +306,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_probe_partial(const ProbePartia
         den32[q] = fmaf(o.x, o.x, fmaf(o.y, o.y, den32[q]));
 #pragma unroll
         for (int k = 0; k < MAXM; ++k)
-          if (k < M) acc[q][k] = cadd(acc[q][k], cconjmul(o, st[k * TP + q * kThreads + threadIdx.x]));
+          if (k < M)
+            acc[q][k] = cadd(acc[q][k], cconjmul(o, psi_ld(reinterpret_cast<const PsiT*>(st + k * TP) +
+                                                            q * kThreads + threadIdx.x)));
       }
       ++consumed;
       if ((v & 31) == 31) {
@@ -405,7 +409,8 @@ __global__ void __launch_bounds__(kThreads) k_probe_div(const ProbeFinalArgs a) 
 // Small kernels.
 // ---------------------------------------------------------------------------
 // psi_j^k(u) = P_k(u) O(r_j + u): the initial fields (Sec. II, first step).
-__global__ void __launch_bounds__(kThreads) k_init_psi(float2* psi, const float2* probe, const float2* obj,
+template <class PsiT>
+__global__ void __launch_bounds__(kThreads) k_init_psi(PsiT* psi, const float2* probe, const float2* obj,
                                                        const int2* pos, int N, int M, int J, int W) {
   // one warp per (view, mode, row); each lane forms two adjacent values and
   // writes them with one 16-byte streaming store (N is even, rows 16-byte
@@ -420,12 +425,17 @@ __global__ void __launch_bounds__(kThreads) k_init_psi(float2* psi, const float2
     const int2 p = pos[j];
     const float2* prow = probe + ((size_t)k * N + y) * N;
     const float2* orow = obj + (size_t)(p.x + y) * W + p.y;
-    float2* dst = psi + (size_t)r * N;
+    PsiT* dst = psi + (size_t)r * N;
     for (int x = 2 * lane; x < N; x += 64) {
       const float4 pv = *reinterpret_cast<const float4*>(prow + x);
       const float2 a = cmul(make_float2(pv.x, pv.y), orow[x]);
       const float2 b = cmul(make_float2(pv.z, pv.w), orow[x + 1]);
-      __stcs(reinterpret_cast<float4*>(dst + x), make_float4(a.x, a.y, b.x, b.y));
+      if constexpr (sizeof(PsiT) == sizeof(float2)) {
+        __stcs(reinterpret_cast<float4*>(dst + x), make_float4(a.x, a.y, b.x, b.y));
+      } else {
+        psi_stcs(dst + x, a);
+        psi_stcs(dst + x + 1, b);
+      }
     }
   }
 }
@@ -561,6 +571,16 @@ cudaError_t launch_wait_selftest(const int* flag, int* status, int* ok, cudaStre
   return cudaGetLastError();
 }
 
+// Exit waves between complex64 and complex half (round to nearest even).
+__global__ void __launch_bounds__(kThreads) k_psi_to_half(__half2* dst, const float2* src, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kThreads)
+    dst[i] = __float22half2_rn(src[i]);
+}
+__global__ void __launch_bounds__(kThreads) k_psi_to_float(float2* dst, const __half2* src, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kThreads)
+    dst[i] = __half22float2(src[i]);
+}
+
 static int grid_for(size_t work, int cap) {
   size_t g = (work + kThreads - 1) / kThreads;
   if (g < 1) g = 1;
@@ -582,26 +602,46 @@ cudaError_t launch_obj_final64(const ObjFinal64Args& a, int blocks, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_obj_source(float2* cview, const float2* psi, const float2* probe, int N, int M, int J,
+cudaError_t launch_obj_source(float2* cview, const void* psi, int psi16, const float2* probe, int N, int M, int J,
                               cudaStream_t s) {
-  k_obj_source<<<grid_for((size_t)J * N * N, 4096), kThreads, 0, s>>>(cview, psi, probe, N, M, J);
+  if (psi16)
+    k_obj_source<<<grid_for((size_t)J * N * N, 4096), kThreads, 0, s>>>(cview, static_cast<const __half2*>(psi), probe,
+                                                                       N, M, J);
+  else
+    k_obj_source<<<grid_for((size_t)J * N * N, 4096), kThreads, 0, s>>>(cview, static_cast<const float2*>(psi), probe,
+                                                                       N, M, J);
   return cudaGetLastError();
 }
 
-template <int MAXM, int PX>
+cudaError_t launch_psi_convert(void* dst, const void* src, size_t n, int to_half, cudaStream_t s) {
+  if (to_half) k_psi_to_half<<<grid_for(n, 8192), kThreads, 0, s>>>(static_cast<__half2*>(dst), static_cast<const float2*>(src), n);
+  else k_psi_to_float<<<grid_for(n, 8192), kThreads, 0, s>>>(static_cast<float2*>(dst), static_cast<const __half2*>(src), n);
+  return cudaGetLastError();
+}
+
+template <int MAXM, int PX, class PsiT>
 static cudaError_t probe_partial_launch(const ProbePartialArgs& a, int num_sms, cudaStream_t s) {
   const size_t smem = probe_partial_smem_bytes(a.M);
   // the limit is shared by every context using this instance: allow the
   // largest mode count the instance serves
-  const void* f = (const void*)k_probe_partial<MAXM, PX>;
+  const void* f = (const void*)k_probe_partial<MAXM, PX, PsiT>;
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)probe_partial_smem_bytes(MAXM));
   if (e != cudaSuccess) return e;
   const int tp = PX * kThreads;
   const int items = ((a.N * a.N + tp - 1) / tp) * a.groups;
   // two CTAs per SM: one CTA's per-view barrier overlaps the other's sums
-  k_probe_partial<MAXM, PX><<<std::min(items, 2 * num_sms), kThreads, smem, s>>>(a);
+  k_probe_partial<MAXM, PX, PsiT><<<std::min(items, 2 * num_sms), kThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <class PsiT>
+static cudaError_t probe_partial_launch_t(const ProbePartialArgs& a, int num_sms, cudaStream_t s) {
+  if (a.M <= 1) return probe_partial_launch<1, kProbePxPerThread, PsiT>(a, num_sms, s);
+  if (a.M <= 2) return probe_partial_launch<2, kProbePxPerThread, PsiT>(a, num_sms, s);
+  if (a.M <= 4) return probe_partial_launch<4, kProbePxPerThread, PsiT>(a, num_sms, s);
+  if (a.M <= 8) return probe_partial_launch<8, kProbePxPerThread, PsiT>(a, num_sms, s);
+  return probe_partial_launch<16, 1, PsiT>(a, num_sms, s);
 }
 
 int probe_tile_px(int M) { return (M > 8 ? 1 : kProbePxPerThread) * kThreads; }
@@ -613,22 +653,25 @@ size_t probe_partial_smem_bytes(int M) {
 // Sets the dynamic shared-memory limit of the probe-partial kernel for M
 // modes ahead of any launch (so that no attribute is set while a stream is
 // being captured).
-cudaError_t prepare_probe_partial(int M) {
+template <class PsiT>
+static cudaError_t prepare_probe_partial_t(int M) {
   const int maxm = M <= 1 ? 1 : M <= 2 ? 2 : M <= 4 ? 4 : M <= 8 ? 8 : 16;
-  const void* f = M <= 1   ? (const void*)k_probe_partial<1, kProbePxPerThread>
-                  : M <= 2 ? (const void*)k_probe_partial<2, kProbePxPerThread>
-                  : M <= 4 ? (const void*)k_probe_partial<4, kProbePxPerThread>
-                  : M <= 8 ? (const void*)k_probe_partial<8, kProbePxPerThread>
-                           : (const void*)k_probe_partial<16, 1>;
+  const void* f = M <= 1   ? (const void*)k_probe_partial<1, kProbePxPerThread, PsiT>
+                  : M <= 2 ? (const void*)k_probe_partial<2, kProbePxPerThread, PsiT>
+                  : M <= 4 ? (const void*)k_probe_partial<4, kProbePxPerThread, PsiT>
+                  : M <= 8 ? (const void*)k_probe_partial<8, kProbePxPerThread, PsiT>
+                           : (const void*)k_probe_partial<16, 1, PsiT>;
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)probe_partial_smem_bytes(maxm));
 }
 
+// Both exit-wave forms, so that a context may switch between them later.
+cudaError_t prepare_probe_partial(int M) {
+  cudaError_t e = prepare_probe_partial_t<float2>(M);
+  return e == cudaSuccess ? prepare_probe_partial_t<__half2>(M) : e;
+}
+
 cudaError_t launch_probe_partial(const ProbePartialArgs& a, int num_sms, cudaStream_t s) {
-  if (a.M <= 1) return probe_partial_launch<1, kProbePxPerThread>(a, num_sms, s);
-  if (a.M <= 2) return probe_partial_launch<2, kProbePxPerThread>(a, num_sms, s);
-  if (a.M <= 4) return probe_partial_launch<4, kProbePxPerThread>(a, num_sms, s);
-  if (a.M <= 8) return probe_partial_launch<8, kProbePxPerThread>(a, num_sms, s);
-  return probe_partial_launch<16, 1>(a, num_sms, s);
+  return a.psi16 ? probe_partial_launch_t<__half2>(a, num_sms, s) : probe_partial_launch_t<float2>(a, num_sms, s);
 }
 
 cudaError_t launch_probe_sum(const ProbeFinalArgs& a, cudaStream_t s) {
@@ -675,11 +718,12 @@ cudaError_t launch_max_f64(const double* x, size_t n, unsigned long long* bits, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_psi(float2* psi, const float2* probe, const float2* obj, const int2* pos, int N, int M,
-                            int J, int W, cudaStream_t s) {
+cudaError_t launch_init_psi(void* psi, int psi16, const float2* probe, const float2* obj, const int2* pos, int N,
+                            int M, int J, int W, cudaStream_t s) {
   const long long rows = (long long)J * M * N;
   const int blocks = (int)std::min<long long>((rows + kThreads / 32 - 1) / (kThreads / 32), 8192);
-  k_init_psi<<<blocks, kThreads, 0, s>>>(psi, probe, obj, pos, N, M, J, W);
+  if (psi16) k_init_psi<<<blocks, kThreads, 0, s>>>(static_cast<__half2*>(psi), probe, obj, pos, N, M, J, W);
+  else k_init_psi<<<blocks, kThreads, 0, s>>>(static_cast<float2*>(psi), probe, obj, pos, N, M, J, W);
   return cudaGetLastError();
 }
 

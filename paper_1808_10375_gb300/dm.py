@@ -25,6 +25,7 @@ DM_HOST, DM_DEVICE = 0, 1
 DM_STEP_FOURIER, DM_STEP_OBJECT, DM_STEP_PROBE = 0, 1, 2
 DM_DFT_FP32, DM_DFT_BF16X3 = 0, 1
 DM_ORDER_GAUSS_SEIDEL, DM_ORDER_JACOBI = 0, 1
+DM_PSI_FP32, DM_PSI_FP16 = 0, 1
 (DM_KERNEL_FOURIER, DM_KERNEL_OBJECT_GATHER, DM_KERNEL_OBJECT_FINAL, DM_KERNEL_PROBE_PARTIAL,
  DM_KERNEL_PROBE_FINAL, DM_KERNEL_METRICS, DM_KERNEL_OTHER, DM_KERNEL_COUNT) = range(8)
 
@@ -43,6 +44,8 @@ class dm_params(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("scratch_bytes", ctypes.c_int64),
         ("update_order", ctypes.c_int32),
+        ("psi_precision", ctypes.c_int32),
+        ("psi_switch", ctypes.c_double),
     ]
 
 
@@ -59,7 +62,7 @@ EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_
            "dm_object_partials", "dm_object_apply", "dm_probe_partials", "dm_probe_apply",
            "dm_fourier_error_partials", "dm_finish_iteration", "dm_set_graph", "dm_autotune",
            "dm_get_plan", "dm_batch_create", "dm_batch_iterate", "dm_batch_set_graph", "dm_batch_free",
-           "dm_batch_last_error", "dm_dft2", "dm_fp32_peak", "dm_net_create", "dm_net_param_count", "dm_net_get_params",
+           "dm_batch_last_error", "dm_dft2", "dm_fp32_peak", "dm_set_psi_precision", "dm_get_psi_precision", "dm_net_create", "dm_net_param_count", "dm_net_get_params",
            "dm_net_set_params", "dm_net_forward", "dm_net_gradients", "dm_net_train_step", "dm_net_free"]
 
 _lib = None
@@ -90,6 +93,8 @@ def load(path: str = LIB_PATH):
         "dm_set_psi_error": (ctypes.c_int, [vp, i32]),
         "dm_selftest_bounded_waits": (ctypes.c_int, [dp]),
         "dm_fp32_peak": (ctypes.c_int, [dp]),
+        "dm_set_psi_precision": (ctypes.c_int, [vp, i32]),
+        "dm_get_psi_precision": (ctypes.c_int, [vp, P(ctypes.c_int32), P(ctypes.c_int64)]),
         "dm_get_psi_error": (ctypes.c_int, [vp, i32, dp]),
         "dm_iterations_done": (i64, [vp]),
         "dm_get_mode_power": (ctypes.c_int, [vp, dp]),
@@ -585,6 +590,20 @@ def dm_get_psi_error(ctx: Context, iteration: int = -1) -> float:
     out = ctypes.c_double()
     _check(load().dm_get_psi_error(ctx.handle, int(iteration), ctypes.byref(out)), ctx)
     return out.value
+
+
+def dm_set_psi_precision(ctx: Context, precision: int):
+    """Convert the exit waves to DM_PSI_FP32 or DM_PSI_FP16 storage (see dm.h)."""
+    return _check(load().dm_set_psi_precision(ctx.handle, int(precision)), ctx)
+
+
+def dm_get_psi_precision(ctx: Context):
+    """(current exit-wave storage, iteration count of the automatic switch to
+    complex64 or -1)."""
+    prec = ctypes.c_int32()
+    at = ctypes.c_int64()
+    _check(load().dm_get_psi_precision(ctx.handle, ctypes.byref(prec), ctypes.byref(at)), ctx)
+    return prec.value, at.value
 
 
 def dm_fp32_peak() -> float:

@@ -153,3 +153,24 @@ def test_static_probe_update_binding_rejects_bad_tensors():
             dm._static_probe_args(**args)
     with pytest.raises(ValueError, match="CUDA"):
         dm._static_probe_args(**good)
+
+
+def test_psi_precision_parameters_are_checked():
+    """dm_init rejects an unknown exit-wave storage, the half form for frame
+    sizes without one, and a negative switch threshold (no GPU needed: the
+    checks come before any CUDA call)."""
+    from paper_1808_10375_gb300 import dm
+    lib = dm.load()
+    pos = np.zeros((1, 2), np.int32)
+    inten = np.zeros((1, 16, 16), np.float32)
+    pr = np.zeros((1, 16, 16), np.complex64)
+    ob = np.zeros((16, 16), np.complex64)
+    for kw, msg in [(dict(psi_precision=7), "psi_precision"), (dict(psi_precision=dm.DM_PSI_FP16), "complex-half"),
+                    (dict(psi_switch=-1.0), "psi_switch")]:
+        params = dm.dm_params_default(n=16, modes=1, views=1, obj_h=16, obj_w=16, **kw)
+        h = ctypes.c_void_p()
+        rc = lib.dm_init(ctypes.byref(h), ctypes.byref(params), pos.ctypes.data, inten.ctypes.data, pr.ctypes.data,
+                         ob.ctypes.data)
+        assert rc == dm.DM_EINVAL and msg in dm.dm_last_error(None), (kw, dm.dm_last_error(None))
+    p = dm.dm_params_default()
+    assert p.psi_precision == dm.DM_PSI_FP32 and p.psi_switch == 0.0

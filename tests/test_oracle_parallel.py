@@ -49,3 +49,19 @@ def test_process_driver_without_stored_exit_waves():
         got = pdm.iterate()
     assert rel(pdm.obj, o1) <= 1e-13 and rel(pdm.probe, p1) <= 1e-13
     assert abs(got["fourier_err"] - want["fourier_err"]) <= 1e-12 * want["fourier_err"]
+
+
+def test_process_driver_rounded_start():
+    """round_start=True equals the oracle iteration from exit waves rounded to
+    complex half (the start of the mixed-precision form)."""
+    s = make_scan(dict(n=32, modes=2, grid=(4, 5), step=7, jitter=1, obj=(70, 80), probe="hg", fwhm=14.0,
+                       photons=1e6, seed=11))
+    p0, o0 = initial_guess(s, np.random.default_rng(11), kind="perturbed")
+    probe, obj = p0.astype(np.complex128), o0.astype(np.complex128)
+    inten = np.asarray(s.intensities, np.float32)
+    psi = odm.init_exit_waves(probe, obj, s.pos)
+    psi = psi.real.astype(np.float16).astype(np.float64) + 1j * psi.imag.astype(np.float16).astype(np.float64)
+    _, p1, o1, _ = odm.dm_iteration(psi, probe, obj, s.pos, inten.astype(np.float64))
+    with ProcessDM(inten, s.pos, probe, obj, workers=2, keep_psi=False, round_start=True) as pdm:
+        pdm.iterate()
+    assert rel(pdm.obj, o1) <= 1e-13 and rel(pdm.probe, p1) <= 1e-13
