@@ -65,13 +65,15 @@ def parse():
     ap.add_argument("--ref-views-per-core", type=int, default=16,
                     help="--impl reference: views per worker process in each step's sample")
     ap.add_argument("--tte-iters", type=int, default=3000, help="tte: iteration limit of each DM run")
+    ap.add_argument("--batch-iters", type=int, default=200, help="batch16: iterations of the convergence comparison")
     ap.add_argument("--tte-psi-switch", type=float, default=5e-5,
                     help="tte: Eq. 6 object change below which the mixed form returns to complex64 exit waves")
     ap.add_argument("--tte-train-steps", type=int, default=3000, help="tte: training steps of the warm-start "
                     "network (0: no warm-started run)")
-    ap.add_argument("--workload", choices=["mm256", "batch16", "dft256", "warmstart", "embed", "tte"],
+    ap.add_argument("--workload", choices=["mm256", "mm128", "batch16", "dft256", "warmstart", "embed", "tte"],
                     default="mm256",
-                    help="mm256: the 8-mode 256x256 scan (the headline); batch16: sixteen uneven scans "
+                    help="mm256: the 8-mode 256x256 scan (the headline); mm128: the 4-mode 128x128 scan "
+                         "(2,500 views); batch16: sixteen uneven scans "
                          "advanced as one batch; dft256: the batched 2-D DFT in both precision forms; "
                          "warmstart: train the warm-start network, judge its start with DM; embed: the "
                          "object embedding fused into the exit-wave update against a separate pass; tte: "
@@ -164,10 +166,17 @@ def gpu_index(local):
     return local
 
 
-def make_inputs(views, device):
+WORKLOADS = {
+    "mm256": WORKLOAD_DESC,
+    "mm128": ("4-mode difference map, 128x128 frames, 50x50 scan (2,500 views) at 10 px, 640x640 object, "
+              "Hermite-Gauss probe modes 0.6/0.25/0.1/0.05, 1e7 photons/frame, FP32"),
+}
+
+
+def make_inputs(views, device, name=WORKLOAD):
     import torch
     from synth import make_scan, initial_guess
-    s = make_scan(WORKLOAD, backend="torch", device=device, views=views)
+    s = make_scan(name, backend="torch", device=device, views=views)
     rng = np.random.default_rng(s.meta["seed"] + 1)
     p0, o0 = initial_guess(s, rng, kind="perturbed")
     return s, p0.astype(np.complex64), o0.astype(np.complex64)
@@ -178,7 +187,7 @@ def kernel_source_hash():
     is used only while it matches."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("dm_fourier.cu", "dm_fft.cuh", "dm_kernels.h"):
+    for f in ("dm_fourier.cu", "dm_fft.cuh", "dm_kernels.h", "dm_psi.cuh", "dm_ptx.cuh"):
         with open(os.path.join(ROOT, "paper_1808_10375_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -359,9 +368,12 @@ def run_reference(args, world, rank):
 
 def run_batch16(args, rank, local):
     """Sixteen uneven scans: each run alone (dm_iterate, one after another)
-    and as one batch (one persistent Fourier launch per frame size, CUDA-graph
-    replay), after each context's autotuner has picked its Fourier plan.  The
-    value is the batch's view*modes per second over all scans."""
+    and as one batch (one persistent Fourier launch per frame size,
+    CUDA-graph replay), after each context's autotuner has picked its Fourier
+    plan.  The value is the batch's view*modes per second over all scans.
+    Also: the per-scan convergence over --batch-iters iterations, batched
+    against alone (Eq. 6 and the Fourier error of every iteration, final
+    object and probe)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -433,6 +445,48 @@ def run_batch16(args, rank, local):
     plans = [dm.dm_get_plan(c) for c in ctxs]
     for c in ctxs:
         dm.dm_free(c)
+
+    # per-scan convergence over args.batch_iters iterations: every scan run
+    # alone and the sixteen advanced together by the batch, from the same start
+    def fresh():
+        out = []
+        for cfg in batch16_configs():
+            sc = make_scan_cfg(cfg)
+            rng = np.random.default_rng(cfg["seed"] + 1)
+            p0, o0 = initial_guess(sc, rng, kind="perturbed")
+            h, w = sc.obj_shape
+            params = dm.dm_params_default(n=sc.n, modes=sc.modes, views=sc.views, obj_h=h, obj_w=w, beta=0.8)
+            dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            out.append(dm.dm_init(params, dev(sc.pos), sc.intensities, dev(p0.astype(np.complex64)),
+                                  dev(o0.astype(np.complex64))))
+        return out
+    hist = lambda c, n: [dm.dm_get_error(c, i) for i in range(n)]
+    nb = args.batch_iters
+    alone = fresh()
+    for c in alone:
+        dm.dm_iterate(c, nb)
+    h_alone = [hist(c, nb) for c in alone]
+    fin_alone = [(dm.dm_get_object(c), dm.dm_get_probe(c)) for c in alone]
+    for c in alone:
+        dm.dm_free(c)
+    together = fresh()
+    bt = dm.dm_batch_create(together)
+    dm.dm_batch_iterate(bt, nb)
+    dm.dm_batch_free(bt)
+    h_tog = [hist(c, nb) for c in together]
+    fin_tog = [(dm.dm_get_object(c), dm.dm_get_probe(c)) for c in together]
+    for c in together:
+        dm.dm_free(c)
+    convergence = []
+    for i in range(len(h_alone)):
+        d_eo = max(abs(a[0] - b_[0]) / max(abs(a[0]), 1e-300) for a, b_ in zip(h_alone[i], h_tog[i]))
+        d_ef = max(abs(a[2] - b_[2]) / max(abs(a[2]), 1e-300) for a, b_ in zip(h_alone[i], h_tog[i]))
+        convergence.append({
+            "scan": i, "eps_obj_first": h_alone[i][0][0], "eps_obj_last": h_alone[i][-1][0],
+            "fourier_err_first": h_alone[i][0][2], "fourier_err_last": h_alone[i][-1][2],
+            "max_rel_diff_eps_obj": d_eo, "max_rel_diff_fourier_err": d_ef,
+            "object_identical": bool(np.array_equal(fin_alone[i][0], fin_tog[i][0])),
+            "probe_identical": bool(np.array_equal(fin_alone[i][1], fin_tog[i][1]))})
     if rank == 0:
         line = {
             "metric": METRIC + ", sixteen scans batched", "value": total_vm * args.steps / t_batch, "unit": UNIT,
@@ -450,6 +504,9 @@ def run_batch16(args, rank, local):
                         "batched_over_alone": ts_alone / ts_batch, "unit": UNIT},
             "fourier_err_last": ferr,
             "plans": plans,
+            "convergence": {"iterations": nb, "how": "each scan alone (dm_iterate) and all sixteen in one batch "
+                                                    "(dm_batch_iterate), from the same inputs; monitors of every "
+                                                    "iteration compared", "scans": convergence},
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
@@ -655,11 +712,11 @@ def run_tte(args, rank, local):
     is the true one and stays fixed: with the probe free, a linear phase ramp
     moved from the object to the probe changes no intensity, so the object
     would be fixed only up to that ramp.  Starts: a random object (white
-    amplitude in [0.5, 1] and phase in [-pi/2, pi/2], seeded), the flat
+    amplitude in [0.5, 1] and phase in [-pi/2, pi/2], three seeds), the flat
     object, and the judged warm start (the network trained here, stitched,
     with DM's Fourier error after 10 trial iterations choosing between it and
     the flat start).  Runs: FP32 from each start, the mixed form from the
-    random and the judged start.  Device seconds are CUDA-event time of the
+    random starts and the judged start.  Device seconds are CUDA-event time of the
     iterations (for the mixed form including its per-iteration check of the
     switch); the object is copied back and scored every 10 iterations
     outside it."""
@@ -678,10 +735,11 @@ def run_tte(args, rank, local):
     for r, c in scan.pos:
         den[r:r + n, c:c + n] += p2
     covered = den >= 0.1 * den.max()
-    rng = np.random.Generator(np.random.PCG64(2002))
-    starts = {"flat": np.ones((h, w), np.complex64),
-              "random": ((0.5 + 0.5 * rng.random((h, w))) *
-                         np.exp(1j * np.pi * (rng.random((h, w)) - 0.5))).astype(np.complex64)}
+    starts = {"flat": np.ones((h, w), np.complex64)}
+    for k, seed in enumerate((2002, 2003, 2004)):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        starts["random" if k == 0 else f"random{k}"] = ((0.5 + 0.5 * rng.random((h, w))) * np.exp(
+            1j * np.pi * (rng.random((h, w)) - 0.5))).astype(np.complex64)
     train_info = None
     starts["judged"] = starts["flat"]
     if args.tte_train_steps > 0:
@@ -706,6 +764,8 @@ def run_tte(args, rank, local):
     arms = [("fp32_random", "random", dm.DM_PSI_FP32), ("fp32_flat", "flat", dm.DM_PSI_FP32),
             ("fp32_judged", "judged", dm.DM_PSI_FP32), ("mixed_random", "random", dm.DM_PSI_FP16),
             ("mixed_judged", "judged", dm.DM_PSI_FP16)]
+    for k in (1, 2):   # two more random starts in both forms: the spread of the slow phase
+        arms += [(f"fp32_random{k}", f"random{k}", dm.DM_PSI_FP32), (f"mixed_random{k}", f"random{k}", dm.DM_PSI_FP16)]
     runs = {}
     with ClockSampler(gpu_index(local)) as clk:
         for name, start, prec in arms:
@@ -817,7 +877,9 @@ def main():
     __graft_entry__.build()
     from paper_1808_10375_gb300 import dm
 
-    s, p0, o0 = make_inputs(args.views, "cuda")
+    wname = args.workload if args.workload in WORKLOADS else WORKLOAD
+    wdesc = WORKLOADS[wname]
+    s, p0, o0 = make_inputs(args.views, "cuda", wname)
     n, m, j = s.n, s.modes, s.views
     h, w = s.obj_shape
     params = dm.dm_params_default(n=n, modes=m, views=j, obj_h=h, obj_w=w, beta=0.8,
@@ -859,7 +921,8 @@ def main():
     fp32_peak = dm.dm_fp32_peak()
     fft_tflops = fourier_flops_per_view(n, m) * j / launch_s / 1e12 if f_n else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": (achieved / hbm) if achieved else None, "traffic": stored_traffic(j),
+                "frac": (achieved / hbm) if achieved else None,
+                "traffic": stored_traffic(j) if wname == WORKLOAD else None,
                 "kernel": "k_fourier (persistent Fourier step, Eq. 3)", "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": f_bytes, "avg_launch_ms": f_ms / f_n if f_n else None,
                 "object_source_bytes_per_launch": c_bytes,
@@ -914,7 +977,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.psi == "fp32" else "f32 arithmetic, exit waves stored as f16", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC if args.views is None else f"{WORKLOAD_DESC} (first {j} views)",
+            "config": {"workload": wdesc if args.views is None else f"{wdesc} (first {j} views)",
                        "n": n, "modes": m, "views": j, "object": [h, w], "beta": 0.8,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (exit waves %.1f GB)" % (j * m * n * n * 8 / 1e9),
