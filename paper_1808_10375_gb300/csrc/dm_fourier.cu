@@ -42,16 +42,25 @@ struct FCfg {
   // row k1 at column t, pass 2 reads column tt of rows t' + R2 d, and both
   // are bank-conflict free with constant offsets from a per-thread base.
   static constexpr int XP = R1 * (R2 + 1);
+  // Per-group strides of the exchange buffers and of the plain rows.  A warp
+  // holds 32 / R2 groups, each touching R2 consecutive 8-byte values at a
+  // time; strides congruent to R2 modulo 16 values (128 bytes, the 32 banks)
+  // put the groups of a warp on different banks.  At R2 = 16 one group
+  // covers all banks and the strides stay as they are.
+  static constexpr int XS = XP + (((R2 - XP) % 16) + 16) % 16;
+  static constexpr int NS = N + (((R2 - N) % 16) + 16) % 16;
+  static_assert(XS % 2 == 0 && NS % 2 == 0, "row buffers start on 16-byte boundaries");
 };
 
 // Row buffers of the row tasks, per group g of R2 lanes: the exchange
-// buffer (padded, XP values), then two plain rows of N values.
+// buffer (padded, XP values in a slot of XS), then two plain rows of N
+// values (in slots of NS).
 template <int N>
-__device__ __forceinline__ float2* row_xbuf(float2* stage, int g) { return stage + g * FCfg<N>::XP; }
+__device__ __forceinline__ float2* row_xbuf(float2* stage, int g) { return stage + g * FCfg<N>::XS; }
 template <int N>
 __device__ __forceinline__ float2* row_buf(float2* stage, int g, int i) {
   using C = FCfg<N>;
-  return stage + C::GR * C::XP + (i * C::GR + g) * N;
+  return stage + C::GR * C::XS + (i * C::GR + g) * C::NS;
 }
 
 // ------------------------------------------------------------------ R task
@@ -889,7 +898,7 @@ template <int N>
 static size_t smem_for(int M, int bufs, int G) {
   using C = FCfg<N>;
   static_assert(tw_entries<N>() * sizeof(float2) <= kTwBytes, "twiddle tables exceed their shared area");
-  const size_t rows = sizeof(float2) * (size_t)C::GR * (C::XP + 2 * N);   // three row buffers per transform
+  const size_t rows = sizeof(float2) * (size_t)C::GR * (C::XS + 2 * C::NS);   // three row buffers per transform
   const bool multi = M > CCfg<N>::SLOTS;
   const size_t cols = sizeof(float2) * (size_t)bufs * G * M * N * kStripW  // strips
                       + sizeof(float) * (size_t)bufs * G * N * kStripW     // their intensities
