@@ -410,11 +410,18 @@ int dm_dft2(const float* in, float* work, float* out, int32_t n, int32_t frames,
  * x 64, float).  The paper has no network; it notes that the starting guess
  * may come from prior results (Sec. III).  Plain DM stays the judge of the
  * reconstruction that starts from the network's stitched prediction.
- * Encoder 1->16->32->64->128->256 channels (3 x 3, stride 2, ReLU; 128 -> 4
- * pixels), decoder with nearest 2x upsampling 256->128->64->32->16 (3 x 3,
- * ReLU; 4 -> 64 pixels), head 16->2 (3 x 3, linear).  Weights are BF16 in
- * every product, with FP32 master copies, activations, gradients and
- * accumulation; the loss is the mean squared error; updates are Adam.
+ * Six levels, 1,964,690 parameters: encoder 1->16->32->64->128->256->256
+ * channels (3 x 3, stride 2, ReLU; 128 -> 2 pixels), decoder with nearest 2x
+ * upsampling 256->256->128->64->32->16 (3 x 3, ReLU; 2 -> 64 pixels), head
+ * 16->2 (3 x 3, linear).  Weights are BF16 in every product, with FP32
+ * master copies, activations, gradients and accumulation; updates are Adam.
+ * The loss (dm_net_set_loss) is the mean squared error over both output
+ * channels (DM_NET_LOSS_MSE, the default) or the phase-gauge-invariant loss
+ * (DM_NET_LOSS_GAUGE): one view's intensities do not change when its object
+ * patch is multiplied by a constant phase factor, so each predicted complex
+ * patch z = a exp(i phi) is compared with its target t after the best global
+ * phase, (sum|z|^2 + sum|t|^2 - 2|sum conj(z) t|) per sample, averaged over
+ * the batch's pixels.
  * Parameters are one flat FP32 array, per layer the weights [co][ci][3][3]
  * then the biases [co].  x, y and target are device pointers on the
  * network's device, [batch][1][128][128] and [batch][2][64][64]; grads and
@@ -439,6 +446,9 @@ int dm_net_gradients(dm_net* net, const float* x, const float* target, int32_t b
                      double* loss);
 int dm_net_train_step(dm_net* net, const float* x, const float* target, int32_t batch, float lr,
                       double* loss);
+#define DM_NET_LOSS_MSE 0
+#define DM_NET_LOSS_GAUGE 1
+int dm_net_set_loss(dm_net* net, int32_t kind);
 void dm_net_free(dm_net* net);
 
 /* Release everything the context holds (NULL is ignored). */

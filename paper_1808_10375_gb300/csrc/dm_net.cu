@@ -6,15 +6,21 @@
 // initial guess may come from prior results, Sec. III); DM itself stays the
 // judge of the result.
 //
-// Layers (NCHW, 3 x 3 kernels, zero padding 1):
-//   encoder  1 -> 16 -> 32 -> 64 -> 128 -> 256 channels, stride 2 each
-//            (128 -> 64 -> 32 -> 16 -> 8 -> 4 pixels), ReLU
-//   decoder  nearest 2x upsampling then stride 1: 256 -> 128 -> 64 -> 32 -> 16
-//            (4 -> 8 -> 16 -> 32 -> 64 pixels), ReLU
+// Layers (NCHW, 3 x 3 kernels, zero padding 1), six levels, 1.96 M
+// parameters:
+//   encoder  1 -> 16 -> 32 -> 64 -> 128 -> 256 -> 256 channels, stride 2 each
+//            (128 -> 64 -> 32 -> 16 -> 8 -> 4 -> 2 pixels), ReLU
+//   decoder  nearest 2x upsampling then stride 1:
+//            256 -> 256 -> 128 -> 64 -> 32 -> 16 (2 -> 4 -> ... -> 64 pixels), ReLU
 //   head     16 -> 2 at 64 x 64, linear (amplitude, phase)
 // Weights are BF16 in every forward and backward product (FP32 master copies
 // for the Adam update); activations, gradients and accumulation are FP32.
-// Training loss: mean squared error over the two output channels.
+// Training loss: the mean squared error over the two output channels, or the
+// phase-gauge-invariant loss.  One view's intensities are unchanged when its
+// object patch is multiplied by a constant phase factor, so the second loss
+// compares each predicted complex patch z = a exp(i phi) with its target t
+// after the best global phase: per sample, sum|z|^2 + sum|t|^2 - 2|S| with
+// S = sum conj(z) t, averaged over the pixels of the batch.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -35,7 +41,7 @@ struct NetLayer {
 
 
 static void net_layout(std::vector<NetLayer>& L, long long& nparams) {
-  const int ch[6] = {1, 16, 32, 64, 128, 256};
+  const int ch[7] = {1, 16, 32, 64, 128, 256, 256};
   int h = 128;
   L.clear();
   long long off = 0;
@@ -44,8 +50,8 @@ static void net_layout(std::vector<NetLayer>& L, long long& nparams) {
     off += (long long)co * ci * 9 + co;
     L.push_back(l);
   };
-  for (int i = 0; i < 5; ++i) { add(ch[i], ch[i + 1], h, h / 2, 2, 0, 1); h /= 2; }
-  for (int i = 5; i > 1; --i) { add(ch[i], ch[i - 1], h, 2 * h, 1, 1, 1); h *= 2; }
+  for (int i = 0; i < 6; ++i) { add(ch[i], ch[i + 1], h, h / 2, 2, 0, 1); h /= 2; }
+  for (int i = 6; i > 1; --i) { add(ch[i], ch[i - 1], h, 2 * h, 1, 1, 1); h *= 2; }
   add(16, 2, 64, 64, 1, 0, 0);
   nparams = off;
 }
@@ -169,6 +175,78 @@ __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ y, const 
   if ((threadIdx.x & 31) == 0) atomicAdd(sum, local);
 }
 
+// Gauge-invariant loss, step 1: per sample b (one block each) the sums over
+// its P pixels of conj(z) t, |z|^2 and |t|^2 in FP64, in a fixed order:
+// sums[b] = {Re S, Im S, sum |z|^2, sum |t|^2}.  y and t are [B][2][P] with
+// channel 0 the amplitude and channel 1 the phase.
+__global__ void __launch_bounds__(256) k_gauge_sums(const float* __restrict__ y, const float* __restrict__ t,
+                                                    double* __restrict__ sums, int P) {
+  __shared__ double red[4][256 / 32];
+  const int b = blockIdx.x;
+  const float* ya = y + (size_t)b * 2 * P;
+  const float* ta = t + (size_t)b * 2 * P;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    float sz, cz, st, ct;
+    sincosf(ya[P + p], &sz, &cz);
+    sincosf(ta[P + p], &st, &ct);
+    const double za = ya[p], tb = ta[p];
+    const double zr = za * cz, zi = za * sz, tr = tb * ct, ti = tb * st;
+    acc[0] += zr * tr + zi * ti;   // Re conj(z) t
+    acc[1] += zr * ti - zi * tr;   // Im conj(z) t
+    acc[2] += za * za;
+    acc[3] += tb * tb;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double v = acc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[k][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0.0;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) v += red[threadIdx.x][i];
+    sums[(size_t)b * 4 + threadIdx.x] = v;
+  }
+}
+
+// Step 2: the gradient with respect to (a, phi) of every output value, with
+// w = t conj(S)/|S| (the target turned by the fitted phase) and u = exp(i phi):
+// dL/da = 2 (a - Re(conj(w) u)) / (B P), dL/dphi = 2 a Im(conj(w) u) / (B P);
+// where S = 0 the fitted phase is undefined and w = 0.  Thread 0 of block 0
+// also adds the per-sample losses in sample order into *loss_sum.
+__global__ void __launch_bounds__(256) k_gauge_grad(const float* __restrict__ y, const float* __restrict__ t,
+                                                    const double* __restrict__ sums, float* __restrict__ g, int B,
+                                                    int P, double* loss_sum) {
+  const size_t n = (size_t)B * P;
+  const float scale = 2.f / (float)n;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / P), p = (int)(i % P);
+    const double sr = sums[(size_t)b * 4], si = sums[(size_t)b * 4 + 1];
+    const double mag = sqrt(sr * sr + si * si);
+    const float cr = mag > 0.0 ? (float)(sr / mag) : 0.f, ci = mag > 0.0 ? (float)(-si / mag) : 0.f;   // conj(S)/|S|
+    const size_t o = (size_t)b * 2 * P + p;
+    float sz, cz, st, ct;
+    sincosf(y[o + P], &sz, &cz);
+    sincosf(t[o + P], &st, &ct);
+    const float a = y[o], tb = t[o];
+    const float wr = tb * (ct * cr - st * ci), wi = tb * (ct * ci + st * cr);   // w = t c
+    const float re = wr * cz + wi * sz, im = wr * sz - wi * cz;                 // conj(w) u
+    g[o] = scale * (a - re);
+    g[o + P] = scale * a * im;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < B; ++b) {
+      const double* q = sums + (size_t)b * 4;
+      s += q[2] + q[3] - 2.0 * sqrt(q[0] * q[0] + q[1] * q[1]);
+    }
+    *loss_sum = s;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
                                               const float* __restrict__ g, __nv_bfloat16* __restrict__ pb,
                                               long long n, float lr, float c1, float c2) {
@@ -205,6 +283,8 @@ struct dm_net {
   std::vector<float*> act;    // act[0] input, act[l + 1] output of layer l
   std::vector<float*> grad;   // gradient of the loss w.r.t. act[l]
   double* loss = nullptr;
+  double* gauge = nullptr;    // [max_batch][4] per-sample sums of the gauge-invariant loss
+  int loss_kind = DM_NET_LOSS_MSE;
   long long steps = 0;
   std::string err;
 };
@@ -239,12 +319,28 @@ int net_forward(dm_net* n, const float* x, int B) {
   return DM_OK;
 }
 
-// gradients of the mean squared error into n->g (and the loss into n->loss)
+// The value by which the loss sum in n->loss is divided: the mean squared
+// error averages over every output value, the gauge-invariant loss over the
+// pixels (two output values each).
+double loss_divisor(const dm_net* n, int B) {
+  const double ny = (double)act_elems(n->L.back(), B, true);
+  return n->loss_kind == DM_NET_LOSS_GAUGE ? ny / 2.0 : ny;
+}
+
+// gradients of the chosen loss into n->g (and the loss sum into n->loss)
 int net_backward(dm_net* n, const float* target, int B) {
   const auto& last = n->L.back();
   const size_t ny = act_elems(last, B, true);
-  NET_CUDA(n, cudaMemsetAsync(n->loss, 0, sizeof(double), n->stream));
-  dmk::k_mse<<<dmk::grid_of(ny), 256, 0, n->stream>>>(n->act.back(), target, n->grad.back(), ny, n->loss);
+  if (n->loss_kind == DM_NET_LOSS_GAUGE) {
+    const int P = last.hout * last.wout;
+    dmk::k_gauge_sums<<<B, 256, 0, n->stream>>>(n->act.back(), target, n->gauge, P);
+    NET_CUDA(n, cudaGetLastError());
+    dmk::k_gauge_grad<<<dmk::grid_of((size_t)B * P), 256, 0, n->stream>>>(n->act.back(), target, n->gauge,
+                                                                          n->grad.back(), B, P, n->loss);
+  } else {
+    NET_CUDA(n, cudaMemsetAsync(n->loss, 0, sizeof(double), n->stream));
+    dmk::k_mse<<<dmk::grid_of(ny), 256, 0, n->stream>>>(n->act.back(), target, n->grad.back(), ny, n->loss);
+  }
   NET_CUDA(n, cudaGetLastError());
   for (int i = (int)n->L.size() - 1; i >= 0; --i) {
     const auto& l = n->L[i];
@@ -292,6 +388,7 @@ int dm_net_create(dm_net** out, int32_t max_batch, uint64_t seed) {
   alloc((void**)&n->g, n->np * sizeof(float));
   alloc((void**)&n->pb, n->np * sizeof(__nv_bfloat16));
   alloc((void**)&n->loss, sizeof(double));
+  alloc((void**)&n->gauge, sizeof(double) * 4 * (size_t)max_batch);
   n->act.assign(n->L.size() + 1, nullptr);
   n->grad.assign(n->L.size() + 1, nullptr);
   for (size_t i = 0; i <= n->L.size(); ++i) {
@@ -368,7 +465,7 @@ int dm_net_gradients(dm_net* n, const float* x, const float* target, int32_t bat
   double s = 0.0;
   NET_CUDA(n, cudaMemcpyAsync(&s, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
   NET_CUDA(n, cudaStreamSynchronize(n->stream));
-  if (loss) *loss = s / (double)act_elems(n->L.back(), batch, true);
+  if (loss) *loss = s / loss_divisor(n, batch);
   return DM_OK;
 }
 
@@ -385,7 +482,14 @@ int dm_net_train_step(dm_net* n, const float* x, const float* target, int32_t ba
   if (loss) NET_CUDA(n, cudaMemcpyAsync(&s, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
   // the caller may reuse x and target once the call returns
   NET_CUDA(n, cudaStreamSynchronize(n->stream));
-  if (loss) *loss = s / (double)act_elems(n->L.back(), batch, true);
+  if (loss) *loss = s / loss_divisor(n, batch);
+  return DM_OK;
+}
+
+int dm_net_set_loss(dm_net* n, int32_t kind) {
+  if (!n || n->magic != 0x54454E44u) return DM_EINVAL;
+  if (kind != DM_NET_LOSS_MSE && kind != DM_NET_LOSS_GAUGE) return net_fail(n, DM_EINVAL, "unknown loss");
+  n->loss_kind = kind;
   return DM_OK;
 }
 
@@ -394,7 +498,8 @@ void dm_net_free(dm_net* n) {
   n->magic = 0;
   cudaSetDevice(n->device);
   if (n->stream) {
-    for (void* q : {(void*)n->p, (void*)n->m, (void*)n->v, (void*)n->g, (void*)n->pb, (void*)n->loss})
+    for (void* q : {(void*)n->p, (void*)n->m, (void*)n->v, (void*)n->g, (void*)n->pb, (void*)n->loss,
+                    (void*)n->gauge})
       if (q) cudaFreeAsync(q, n->stream);
     for (float* q : n->act) if (q) cudaFreeAsync(q, n->stream);
     for (float* q : n->grad) if (q) cudaFreeAsync(q, n->stream);

@@ -26,6 +26,7 @@ DM_STEP_FOURIER, DM_STEP_OBJECT, DM_STEP_PROBE = 0, 1, 2
 DM_DFT_FP32, DM_DFT_BF16X3 = 0, 1
 DM_ORDER_GAUSS_SEIDEL, DM_ORDER_JACOBI = 0, 1
 DM_PSI_FP32, DM_PSI_FP16 = 0, 1
+DM_NET_LOSS_MSE, DM_NET_LOSS_GAUGE = 0, 1
 (DM_KERNEL_FOURIER, DM_KERNEL_OBJECT_GATHER, DM_KERNEL_OBJECT_FINAL, DM_KERNEL_PROBE_PARTIAL,
  DM_KERNEL_PROBE_FINAL, DM_KERNEL_METRICS, DM_KERNEL_OTHER, DM_KERNEL_COUNT) = range(8)
 
@@ -63,7 +64,8 @@ EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_
            "dm_fourier_error_partials", "dm_finish_iteration", "dm_set_graph", "dm_autotune",
            "dm_get_plan", "dm_batch_create", "dm_batch_iterate", "dm_batch_set_graph", "dm_batch_free",
            "dm_batch_last_error", "dm_dft2", "dm_fp32_peak", "dm_set_psi_precision", "dm_get_psi_precision", "dm_net_create", "dm_net_param_count", "dm_net_get_params",
-           "dm_net_set_params", "dm_net_forward", "dm_net_gradients", "dm_net_train_step", "dm_net_free"]
+           "dm_net_set_params", "dm_net_forward", "dm_net_gradients", "dm_net_train_step", "dm_net_set_loss",
+           "dm_net_free"]
 
 _lib = None
 
@@ -129,6 +131,7 @@ def load(path: str = LIB_PATH):
         "dm_net_forward": (ctypes.c_int, [vp, vp, i32, vp]),
         "dm_net_gradients": (ctypes.c_int, [vp, vp, vp, i32, f32p, dp]),
         "dm_net_train_step": (ctypes.c_int, [vp, vp, vp, i32, ctypes.c_float, dp]),
+        "dm_net_set_loss": (ctypes.c_int, [vp, i32]),
         "dm_net_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -424,6 +427,12 @@ def dm_net_train_step(net: Net, x, target, lr: float = 1e-3, want_loss: bool = F
     _ncheck(load().dm_net_train_step(net.handle, _cuda_f32(x, (b, 1, 128, 128)), _cuda_f32(target, (b, 2, 64, 64)), b,
                                      float(lr), ctypes.byref(loss) if want_loss else None))
     return loss.value if want_loss else None
+
+
+def dm_net_set_loss(net: Net, kind: int):
+    """The training loss: DM_NET_LOSS_MSE or DM_NET_LOSS_GAUGE (the
+    phase-gauge-invariant loss)."""
+    _ncheck(load().dm_net_set_loss(net.handle, int(kind)))
 
 
 def dm_net_free(net: Net):

@@ -74,18 +74,64 @@ def pairs(count, seed, device="cuda", objects=8, object_side=768, noise=True):
     return x_out, t_out
 
 
-def stitch(pred, pos, obj_shape):
+def footprints(obj, pos):
+    """The N x N footprints [J, N, N] of a complex object (torch tensor) at
+    top-left corners ``pos`` [J, 2]."""
+    import torch
+    dev = obj.device
+    p = torch.as_tensor(np.asarray(pos), device=dev).long()
+    ar = torch.arange(N, device=dev)
+    return obj[p[:, 0, None, None] + ar[None, :, None], p[:, 1, None, None] + ar[None, None, :]]
+
+
+def _unit(s):
+    """s / |s|, and 1 where s = 0."""
+    import torch
+    mag = torch.abs(s)
+    return torch.where(mag > 0, s / torch.clamp(mag, min=1e-30), torch.ones_like(s))
+
+
+def stitch(pred, pos, obj_shape, align=False, sweeps=20):
     """Object start from per-view predictions [J, 2, 64, 64] (amplitude, phase)
     at footprints with top-left corners ``pos`` [J, 2]: overlapping
     predictions are averaged as complex values; pixels no prediction covers
-    are 1."""
+    are 1.
+
+    One view's intensities fix its patch z_j only up to a constant phase
+    factor w_j, so with ``align`` the factors are chosen to make the
+    overlapping patches agree: maximise sum_{j != k} Re(conj(w_j z_j) w_k z_k)
+    summed over the overlaps, the angular synchronisation problem.  Start:
+    each prediction in the order of ``pos`` takes the phase that best fits
+    what the views before it laid down (w_j = S_j/|S_j|, S_j = sum conj(z_j)
+    acc over its patch).  Then ``sweeps`` steps of the projected power method
+    (every w_j at once from the sum of all other aligned patches over its
+    patch), which removes the drift the one-pass start accumulates along the
+    scan.  Last, all patches are turned together so that their sum is real and
+    positive: the pixels no prediction covers keep the value 1, and the
+    predictions must share its phase reference (the objects have mean phase
+    about 0)."""
     import torch
     h, w = obj_shape
     dev = pred.device
-    acc = torch.zeros((h, w), dtype=torch.complex64, device=dev)
-    cnt = torch.zeros((h, w), dtype=torch.float32, device=dev)
     c = (N - PATCH) // 2
     z = pred[:, 0] * torch.exp(1j * pred[:, 1])
+    if align:
+        acc2 = torch.zeros((h, w), dtype=torch.complex64, device=dev)
+        u = torch.empty_like(z)
+        for j in range(pos.shape[0]):
+            r, q = int(pos[j, 0]) + c, int(pos[j, 1]) + c
+            u[j] = z[j] * _unit(torch.sum(torch.conj(z[j]) * acc2[r:r + PATCH, q:q + PATCH]))
+            acc2[r:r + PATCH, q:q + PATCH] += u[j]
+        p = torch.as_tensor(np.asarray(pos), device=dev).long() + c
+        ar = torch.arange(PATCH, device=dev)
+        idx = ((p[:, 0, None, None] + ar[None, :, None]) * w + p[:, 1, None, None] + ar[None, None, :]).reshape(-1)
+        for _ in range(sweeps):
+            acc = torch.zeros(h * w, dtype=torch.complex64, device=dev).index_add_(0, idx, u.reshape(-1))
+            others = acc[idx].reshape(z.shape) - u
+            u = z * _unit(torch.sum(torch.conj(z) * others, dim=(1, 2)))[:, None, None]
+        z = u * torch.conj(_unit(torch.sum(u)))
+    acc = torch.zeros((h, w), dtype=torch.complex64, device=dev)
+    cnt = torch.zeros((h, w), dtype=torch.float32, device=dev)
     for j in range(pos.shape[0]):
         r, q = int(pos[j, 0]) + c, int(pos[j, 1]) + c
         acc[r:r + PATCH, q:q + PATCH] += z[j]

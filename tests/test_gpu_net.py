@@ -47,6 +47,54 @@ def test_forward_and_gradients_match_the_reference():
     dm.dm_net_free(net)
 
 
+def test_gauge_loss_and_gradients_match_the_reference():
+    """The phase-gauge-invariant loss through the network against the FP64
+    reference; turning every target patch by its own constant phase leaves
+    the loss unchanged."""
+    import torch
+    from oracle import net as onet
+    from paper_1808_10375_gb300 import dm
+    from synth import warmstart as ws
+    net = dm.dm_net_create(max_batch=4, seed=5)
+    dm.dm_net_set_loss(net, dm.DM_NET_LOSS_GAUGE)
+    rng = np.random.default_rng(8)
+    p = (onet.he_params(rng) + 0.01 * rng.standard_normal(onet.param_count())).astype(np.float32)
+    dm.dm_net_set_params(net, p)
+    x, t = ws.pairs(3, 9)
+    g, loss = dm.dm_net_gradients(net, x, t)
+    ref_loss, ref_g = onet.loss_and_gradients(p.astype(np.float64), x.cpu().numpy().astype(np.float64),
+                                              t.cpu().numpy().astype(np.float64), loss="gauge")
+    err_g = _rel(g, ref_g)
+    print(f"gauge loss {loss:.6g} vs {ref_loss:.6g}, gradient rel L2 {err_g:.2e}")
+    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    assert err_g <= 1e-4
+    t2 = t.clone()
+    t2[:, 1] += torch.tensor([0.4, -2.0, 3.1], device=t.device)[:, None, None]
+    _, loss2 = dm.dm_net_gradients(net, x, t2)
+    assert abs(loss2 - loss) <= 1e-5 * loss
+    with pytest.raises(dm.DMError):
+        dm.dm_net_set_loss(net, 7)
+    dm.dm_net_free(net)
+
+
+def test_dm_refined_pairs():
+    """One simulated 4-mode scan: every view gives an input frame, a target
+    patch of the object after 20 DM iterations and the true patch; the
+    refined targets are much closer to the truth (after the best phase per
+    patch) than the flat object is."""
+    import torch
+    from paper_1808_10375_gb300 import warmstart
+    x, t, g = warmstart.refined_pairs(1, 4242, dm_iters=20)
+    assert x.shape == (2500, 1, 128, 128) and t.shape == (2500, 2, 64, 64) and g.shape == t.shape
+    assert torch.isfinite(x).all() and torch.isfinite(t).all()
+    flat = torch.zeros_like(g)
+    flat[:, 0] = 1.0
+    err_dm = warmstart.fit_of(t, g)["complex_rel_err_gauge_aligned"]
+    err_flat = warmstart.fit_of(flat, g)["complex_rel_err_gauge_aligned"]
+    print("DM-refined target error", err_dm, "flat", err_flat)
+    assert err_dm < 0.5 * err_flat
+
+
 def test_warm_start_is_trained_and_judged_by_dm():
     """The network trains on simulated pairs with the library's kernels, its
     stitched start is judged by DM's own Fourier error (the start with the
@@ -83,14 +131,16 @@ def test_warm_start_is_trained_and_judged_by_dm():
 
 
 def test_training_is_reproducible():
-    """Two networks from the same seed, trained on the same seeded batches
-    (gathered by torch right before each call, as warmstart.train does), end
+    """Two networks from the same seed, trained with the gauge-invariant loss
+    on the same seeded batches (gathered by torch right before each call, as
+    warmstart.train does), end
     with bit-identical parameters: every network kernel is deterministic, and
     each call waits for its inputs and finishes before returning."""
     from paper_1808_10375_gb300 import dm, warmstart
     params = []
     for _ in range(2):
         net = dm.dm_net_create(max_batch=32, seed=3)
+        dm.dm_net_set_loss(net, dm.DM_NET_LOSS_GAUGE)
         warmstart.train(net, steps=40, batch=32, lr=1e-3, seed=4, data_count=512)
         params.append(dm.dm_net_get_params(net))
         dm.dm_net_free(net)
