@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--views", type=int, default=None, help="use only the first V views (small case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--autotune", type=int, default=0, metavar="V",
+                    help="pick the Fourier-step plan with dm_autotune on the first V views before timing (0: the "
+                         "default plan)")
     ap.add_argument("--psi", choices=["fp32", "fp16"], default="fp32",
                     help="exit-wave storage of the timed iteration (fp16: the mixed-precision form, no switch)")
     ap.add_argument("--cpu-views", type=int, default=600, help="views in the one-process oracle sample")
@@ -581,12 +584,49 @@ def run_dft256(args, rank, local):
         }), flush=True)
 
 
+TRAIN_SCANS = 20        # DM-refined training data: 20 scans x 2,500 views = 50,000 frames
+TRAIN_SEED = 5000
+FRESH_SEED = 9000       # two further scans, never trained on
+
+
+def trained_warm_net(steps):
+    """The warm-start network trained as the learned-start configuration
+    states: 6 levels, 1.96 M parameters, 50,000 frames of 20 simulated 4-mode
+    scans with targets refined by 20 DM iterations, the phase-gauge-invariant
+    loss, ``steps`` Adam steps of 64.  Returns (net, record)."""
+    import torch
+    from paper_1808_10375_gb300 import dm, warmstart
+    t0 = time.perf_counter()
+    x, t, _ = warmstart.refined_pairs(TRAIN_SCANS, TRAIN_SEED, dm_iters=20)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = dm.dm_net_create(max_batch=64, seed=11)
+    dm.dm_net_set_loss(net, dm.DM_NET_LOSS_GAUGE)
+    t0 = time.perf_counter()
+    losses = warmstart.train(net, steps=steps, batch=64, lr=1e-3, seed=12, data=(x, t))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del x, t
+    xf, tf, gf = warmstart.refined_pairs(2, FRESH_SEED, dm_iters=20)
+    rec = {"frames": TRAIN_SCANS * 2500, "scans": TRAIN_SCANS, "targets": "refined by 20 DM iterations",
+           "loss": "phase-gauge invariant", "params": dm.dm_net_param_count(net), "steps": steps,
+           "data_s": t_data, "train_s": t_train, "samples_per_s": steps * 64 / t_train,
+           "loss_first": losses[0][1], "loss_last": losses[-1][1],
+           "fresh_scans": {"frames": int(xf.shape[0]),
+                           "fit_to_dm_refined_targets": warmstart.fit(net, xf, tf),
+                           "fit_to_true_object": warmstart.fit(net, xf, gf),
+                           "dm_refined_target_vs_true_object": warmstart.fit_of(tf, gf)}}
+    del xf, tf, gf
+    torch.cuda.empty_cache()
+    return net, rec
+
+
 def run_warmstart(args, rank, local):
     """The learned warm start: train the encoder-decoder (the library's BF16
-    kernels) on 50,000 simulated pairs, measure its fit on fresh pairs, stitch
-    its start for a 4-mode 128x128 scan (12x12 views, noise-free) and run DM
-    from it and from the flat start; DM's Fourier error after 10 trial
-    iterations picks the start."""
+    kernels) on 50,000 DM-refined frames, measure its fit on the frames of two
+    fresh scans, stitch its start for a 4-mode 128x128 scan (12x12 views,
+    noise-free) and run DM from it and from the flat start; DM's Fourier
+    error after 10 trial iterations picks the start."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -595,17 +635,7 @@ def run_warmstart(args, rank, local):
     from synth import warmstart as ws
     torch.cuda.set_device(local)
     steps = args.steps if args.steps != 30 else 3000
-    net = dm.dm_net_create(max_batch=64, seed=11)
-    t0 = time.perf_counter()
-    losses = warmstart.train(net, steps=steps, batch=64, lr=1e-3, seed=12, data_count=50000)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    x, t = ws.pairs(512, 99)
-    ys = torch.cat([dm.dm_net_forward(net, x[i:i + 64].contiguous()) for i in range(0, 512, 64)])
-    fit = {}
-    for ch, name in ((0, "amplitude"), (1, "phase")):
-        mse = float(((ys[:, ch] - t[:, ch]) ** 2).mean())
-        fit[name] = {"mse": mse, "r2": 1.0 - mse / float(t[:, ch].var())}
+    net, training = trained_warm_net(steps)
     cfg = dict(n=128, modes=4, grid=(12, 12), step=10, jitter=1, obj=(250, 250), probe="hg", fwhm=ws.FWHM,
                photons=ws.PHOTONS, seed=13)
     scan = make_scan(cfg, noise=False)
@@ -624,12 +654,10 @@ def run_warmstart(args, rank, local):
             "unit": "relative L2 object error after 200 iterations", "higher_is_better": False, "n_gpus": 1,
             "dtype": "bf16 weights, fp32 accumulation", "data": "synthetic",
             "config": {"workload": "warm-start network: 1x128x128 diffraction amplitude -> 2x64x64 object patch, "
-                                   f"{steps} Adam steps of 64 on 50,000 simulated pairs; judged on a noise-free "
+                                   f"{steps} Adam steps of 64 on 50,000 DM-refined frames; judged on a noise-free "
                                    "4-mode 128x128 scan, 12x12 views at 10 px, 250x250 object",
                        "params": nparams},
-            "training": {"steps": steps, "seconds": t_train, "samples_per_s": steps * 64 / t_train,
-                         "loss_first": losses[0][1], "loss_last": losses[-1][1]},
-            "fit_on_fresh_pairs": fit, "judge": {"pick": pick, "fourier_error_after_trial": ef}, "runs": runs,
+            "training": training, "judge": {"pick": pick, "fourier_error_after_trial": ef}, "runs": runs,
         }), flush=True)
 
 
@@ -743,18 +771,16 @@ def run_tte(args, rank, local):
     train_info = None
     starts["judged"] = starts["flat"]
     if args.tte_train_steps > 0:
-        net = dm.dm_net_create(max_batch=64, seed=11)
-        t0 = time.perf_counter()
-        warmstart.train(net, steps=args.tte_train_steps, batch=64, lr=1e-3, seed=12, data_count=50000)
-        torch.cuda.synchronize()
-        t_train = time.perf_counter() - t0
+        net, training = trained_warm_net(args.tte_train_steps)
+        t_train = training["data_s"] + training["train_s"]
         t0 = time.perf_counter()
         o_warm = warmstart.predict_start(net, scan.intensities, scan.pos, scan.obj_shape)
         chosen, pick, ef = warmstart.judged_start(scan, scan.probe, o_warm, trial_iters=10)
         t_pick = time.perf_counter() - t0
         dm.dm_net_free(net)
         starts["judged"] = chosen
-        train_info = {"steps": args.tte_train_steps, "train_s": t_train, "predict_and_judge_s": t_pick,
+        train_info = {"steps": args.tte_train_steps, "train_s": t_train, "training": training,
+                      "predict_and_judge_s": t_pick,
                       "judge_pick": pick, "fourier_error_after_trial": ef,
                       "predicted_start_error": ws.object_error(o_warm.detach().cpu().numpy(), scan.obj, covered)}
     stream = torch.cuda.Stream()
@@ -889,6 +915,9 @@ def main():
     torch.cuda.set_stream(stream)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     ctx = dm.dm_init(params, dev(s.pos), s.intensities, dev(p0), dev(o0), stream=stream.cuda_stream)
+    if args.autotune > 0:
+        dm.dm_autotune(ctx, sample_views=min(j, args.autotune))
+    plan = dm.dm_get_plan(ctx)
     dm.dm_iterate(ctx, args.warmup)
     dm.dm_sync(ctx)
 
@@ -964,7 +993,8 @@ def main():
         e2e = {"value": job_throughput(world, j, m, args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "session": f"dm_init from pinned host buffers + {args.steps} iterations + object, probe "
-                          f"and metrics to host, per step = session / {args.steps}"}
+                          f"and metrics to host, per step = session / {args.steps}",
+               "fourier_plan": "default"}
 
     # ---- CPU oracle baseline (rank 0, N = 1) ---------------------------------
     cpu = None
@@ -981,6 +1011,7 @@ def main():
                        "n": n, "modes": m, "views": j, "object": [h, w], "beta": 0.8,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (exit waves %.1f GB)" % (j * m * n * n * 8 / 1e9),
+                       "fourier_plan": dict(plan, autotuned=args.autotune > 0),
                        "iteration_algorithmic_bytes": iter_bytes,
                        "iteration_hbm_frac": iter_bytes / (t_ms / args.steps / 1e3) / 1e9 / hbm},
             "roofline": roofline,
