@@ -134,7 +134,10 @@ cudaError_t launch_obj_final64(const ObjFinal64Args& a, int blocks, cudaStream_t
 // FP64 reduction over the groups and the division.
 // ---------------------------------------------------------------------------
 constexpr int kProbePxPerThread = 2;   // pixels per thread for M <= 8 (1 above)
-constexpr int kProbeStages = 3;        // depth of the views' shared-memory ring (2 CTAs per SM)
+// depth of the views' shared-memory ring (2 CTAs per SM): complex64 exit
+// waves 3 views, complex half (half the bytes per view) 5
+template <class PsiT>
+__host__ __device__ constexpr int probe_stages() { return sizeof(PsiT) == 8 ? 3 : 5; }
 
 struct ProbePartialArgs {
   int N, M, J, H, W, groups;

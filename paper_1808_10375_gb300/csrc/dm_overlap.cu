@@ -216,29 +216,35 @@ __global__ void __launch_bounds__(kThreads) k_obj_source(float2* cview, const Ps
 
 // ---------------------------------------------------------------------------
 // Probe update, part 1 (Eq. 4 numerator and denominator partial sums).
-// Work items are (pixel tile, view group); each thread owns PX pixels of the
-// tile and sums over the group's views
+// Work items are (pixel tile, view group); each thread owns PX adjacent
+// pixels of the tile (read with one vector load per mode) and sums over the
+// group's views
 //   num_k(u) += conj(O(r_j + u)) psi_j^k(u),   den(u) += |O(r_j + u)|^2
 // (num in FP32, den in FP32 over 32 views then FP64), then writes the item's
 // partials.  Persistent CTAs (two per SM) stream the views through a
-// kProbeStages-deep shared-memory ring: one bulk asynchronous copy per mode
-// brings the tile of psi_j^k (contiguous in memory), and each thread copies
-// the object values of its own pixels with 8-byte asynchronous copies, so
-// several views' reads are in flight while one is summed.
+// shared-memory ring of probe_stages<PsiT>() views: one bulk asynchronous
+// copy per mode brings the tile of psi_j^k (contiguous in memory), and each
+// thread copies the object values of its own pixels with 8-byte asynchronous
+// copies, so several views' reads are in flight while one is summed.  A
+// view's time is set by how many views are in flight (the ring's depth)
+// more than by its bytes, so complex-half exit waves, half the bytes per
+// view, get a ring twice as deep in about the same shared memory.
 // ---------------------------------------------------------------------------
 template <int MAXM, int PX, class PsiT>
 __global__ void __launch_bounds__(kThreads, 2) k_probe_partial(const ProbePartialArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[kProbeStages];
+  constexpr int STAGES = probe_stages<PsiT>();
+  __shared__ __align__(8) uint64_t full[STAGES];
   constexpr int TP = PX * kThreads;  // pixels per tile
+  constexpr int MS = TP * (int)sizeof(PsiT) / (int)sizeof(float2);   // float2 slots of one mode's tile
   const int N = a.N, M = a.M;
   const int nn = N * N;
   const int tiles = (nn + TP - 1) / TP;
   const int items = tiles * a.groups;
   float2* ring = reinterpret_cast<float2*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
-  const int stage_elems = (M + 1) * TP;  // M tiles of psi, then the object values
+  const int stage_elems = M * MS + TP;  // M tiles of psi, then the object values
   if (threadIdx.x == 0) {
-    for (int b = 0; b < kProbeStages; ++b) mbar_init(&full[b], 1);
+    for (int b = 0; b < STAGES; ++b) mbar_init(&full[b], 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -251,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_probe_partial(const ProbePartia
     const int nv = j1 - j0;
     const int u0 = tile * TP;
     const int npx = min(TP, nn - u0);               // a multiple of 256 (nn is)
-    const uint32_t mode_bytes = (uint32_t)npx * sizeof(PsiT);   // a mode's tile of psi (its slot holds float2)
+    const uint32_t mode_bytes = (uint32_t)npx * sizeof(PsiT);   // a mode's tile of psi
     int uy[PX], ux[PX];
     bool ok[PX];
     float2 acc[PX][MAXM];
@@ -259,8 +265,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_probe_partial(const ProbePartia
     double den64[PX];
 #pragma unroll
     for (int q = 0; q < PX; ++q) {
-      const int u = u0 + q * kThreads + threadIdx.x;
-      ok[q] = q * kThreads + (int)threadIdx.x < npx;
+      const int u = u0 + PX * threadIdx.x + q;
+      ok[q] = PX * (int)threadIdx.x + q < npx;
       uy[q] = u / N;
       ux[q] = u % N;
       den32[q] = 0.f;
@@ -270,45 +276,61 @@ __global__ void __launch_bounds__(kThreads, 2) k_probe_partial(const ProbePartia
     }
     // view i of the item into the next ring stage (every thread calls this)
     auto issue = [&](int i, int2 p) {
-      float2* st = ring + (size_t)(issued % kProbeStages) * stage_elems;
+      float2* st = ring + (size_t)(issued % STAGES) * stage_elems;
       if (threadIdx.x == 0) {
-        uint64_t* bar = &full[issued % kProbeStages];
+        uint64_t* bar = &full[issued % STAGES];
         mbar_arrive_expect_tx(bar, mode_bytes * (uint32_t)M);
         const PsiT* src = static_cast<const PsiT*>(a.psi) + (size_t)(j0 + i) * M * nn + u0;
-        for (int k = 0; k < M; ++k) bulk_load(st + k * TP, src + (size_t)k * nn, mode_bytes, bar);
+        for (int k = 0; k < M; ++k) bulk_load(st + k * MS, src + (size_t)k * nn, mode_bytes, bar);
       }
 #pragma unroll
       for (int q = 0; q < PX; ++q)
-        if (ok[q]) cp_async8(st + M * TP + q * kThreads + threadIdx.x,
-                             a.obj + (size_t)(p.x + uy[q]) * a.W + p.y + ux[q]);
+        if (ok[q]) cp_async8(st + M * MS + PX * threadIdx.x + q, a.obj + (size_t)(p.x + uy[q]) * a.W + p.y + ux[q]);
       ++issued;
     };
-    // prologue: kProbeStages - 1 views in flight (one commit group each)
-    for (int i = 0; i < kProbeStages - 1; ++i) {
+    // prologue: STAGES - 1 views in flight (one commit group each)
+    for (int i = 0; i < STAGES - 1; ++i) {
       if (i < nv) issue(i, __ldg(a.pos + j0 + i));
       cp_async_commit();
     }
-    int2 p_next = (kProbeStages - 1 < nv) ? __ldg(a.pos + j0 + kProbeStages - 1) : make_int2(0, 0);
+    int2 p_next = (STAGES - 1 < nv) ? __ldg(a.pos + j0 + STAGES - 1) : make_int2(0, 0);
     for (int v = 0; v < nv; ++v) {
-      const int b = consumed % kProbeStages;
-      if (threadIdx.x == 0) mbar_wait_bounded(&full[b], (consumed / kProbeStages) & 1u, a.status);
-      cp_async_wait<kProbeStages - 2>();
+      const int b = consumed % STAGES;
+      if (threadIdx.x == 0) mbar_wait_bounded(&full[b], (consumed / STAGES) & 1u, a.status);
+      cp_async_wait<STAGES - 2>();
       __syncthreads();
       // the stage consumed in the previous step is free for view v + S - 1
-      if (v + kProbeStages - 1 < nv) issue(v + kProbeStages - 1, p_next);
+      if (v + STAGES - 1 < nv) issue(v + STAGES - 1, p_next);
       cp_async_commit();
-      if (v + kProbeStages < nv) p_next = __ldg(a.pos + j0 + v + kProbeStages);
+      if (v + STAGES < nv) p_next = __ldg(a.pos + j0 + v + STAGES);
       const float2* st = ring + (size_t)b * stage_elems;
+      if constexpr (PX == 2) {
+        if (ok[0]) {   // the pair is whole: npx is even
+          float2 o[2];
+          psi_ld2(st + M * MS + 2 * threadIdx.x, o[0], o[1]);
 #pragma unroll
-      for (int q = 0; q < PX; ++q) {
-        if (!ok[q]) continue;
-        const float2 o = st[M * TP + q * kThreads + threadIdx.x];
-        den32[q] = fmaf(o.x, o.x, fmaf(o.y, o.y, den32[q]));
+          for (int q = 0; q < 2; ++q) den32[q] = fmaf(o[q].x, o[q].x, fmaf(o[q].y, o[q].y, den32[q]));
 #pragma unroll
-        for (int k = 0; k < MAXM; ++k)
-          if (k < M)
-            acc[q][k] = cadd(acc[q][k], cconjmul(o, psi_ld(reinterpret_cast<const PsiT*>(st + k * TP) +
-                                                            q * kThreads + threadIdx.x)));
+          for (int k = 0; k < MAXM; ++k)
+            if (k < M) {
+              float2 w0, w1;
+              psi_ld2(reinterpret_cast<const PsiT*>(st + k * MS) + 2 * threadIdx.x, w0, w1);
+              acc[0][k] = cadd(acc[0][k], cconjmul(o[0], w0));
+              acc[1][k] = cadd(acc[1][k], cconjmul(o[1], w1));
+            }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < PX; ++q) {
+          if (!ok[q]) continue;
+          const float2 o = st[M * MS + PX * threadIdx.x + q];
+          den32[q] = fmaf(o.x, o.x, fmaf(o.y, o.y, den32[q]));
+#pragma unroll
+          for (int k = 0; k < MAXM; ++k)
+            if (k < M)
+              acc[q][k] = cadd(acc[q][k], cconjmul(o, psi_ld(reinterpret_cast<const PsiT*>(st + k * MS) +
+                                                              PX * threadIdx.x + q)));
+        }
       }
       ++consumed;
       if ((v & 31) == 31) {
@@ -319,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_probe_partial(const ProbePartia
 #pragma unroll
     for (int q = 0; q < PX; ++q) {
       if (!ok[q]) continue;
-      const int u = u0 + q * kThreads + threadIdx.x;
+      const int u = u0 + PX * threadIdx.x + q;
       a.part_den[(size_t)g * nn + u] = den64[q] + den32[q];
 #pragma unroll
       for (int k = 0; k < MAXM; ++k)
@@ -330,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_probe_partial(const ProbePartia
   // copies that a timed-out wait left in flight land before the CTA exits
   if (threadIdx.x == 0)
     while (consumed < issued) {
-      mbar_wait_bounded(&full[consumed % kProbeStages], (consumed / kProbeStages) & 1u, a.status);
+      mbar_wait_bounded(&full[consumed % STAGES], (consumed / STAGES) & 1u, a.status);
       ++consumed;
     }
   cp_async_wait<0>();
@@ -619,14 +641,20 @@ cudaError_t launch_psi_convert(void* dst, const void* src, size_t n, int to_half
   return cudaGetLastError();
 }
 
+template <class PsiT>
+static size_t probe_partial_smem_t(int M) {
+  const int tp = probe_tile_px(M);
+  return 128 + (size_t)probe_stages<PsiT>() * ((size_t)M * tp * sizeof(PsiT) + (size_t)tp * sizeof(float2));
+}
+
 template <int MAXM, int PX, class PsiT>
 static cudaError_t probe_partial_launch(const ProbePartialArgs& a, int num_sms, cudaStream_t s) {
-  const size_t smem = probe_partial_smem_bytes(a.M);
+  const size_t smem = probe_partial_smem_t<PsiT>(a.M);
   // the limit is shared by every context using this instance: allow the
   // largest mode count the instance serves
   const void* f = (const void*)k_probe_partial<MAXM, PX, PsiT>;
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)probe_partial_smem_bytes(MAXM));
+                                       (int)probe_partial_smem_t<PsiT>(MAXM));
   if (e != cudaSuccess) return e;
   const int tp = PX * kThreads;
   const int items = ((a.N * a.N + tp - 1) / tp) * a.groups;
@@ -646,9 +674,7 @@ static cudaError_t probe_partial_launch_t(const ProbePartialArgs& a, int num_sms
 
 int probe_tile_px(int M) { return (M > 8 ? 1 : kProbePxPerThread) * kThreads; }
 
-size_t probe_partial_smem_bytes(int M) {
-  return 128 + (size_t)kProbeStages * (M + 1) * probe_tile_px(M) * sizeof(float2);
-}
+size_t probe_partial_smem_bytes(int M) { return probe_partial_smem_t<float2>(M); }
 
 // Sets the dynamic shared-memory limit of the probe-partial kernel for M
 // modes ahead of any launch (so that no attribute is set while a stream is
@@ -661,7 +687,7 @@ static cudaError_t prepare_probe_partial_t(int M) {
                   : M <= 4 ? (const void*)k_probe_partial<4, kProbePxPerThread, PsiT>
                   : M <= 8 ? (const void*)k_probe_partial<8, kProbePxPerThread, PsiT>
                            : (const void*)k_probe_partial<16, 1, PsiT>;
-  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)probe_partial_smem_bytes(maxm));
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)probe_partial_smem_t<PsiT>(maxm));
 }
 
 // Both exit-wave forms, so that a context may switch between them later.
