@@ -26,28 +26,20 @@
 #include "dm.h"
 #include "dm_fft.cuh"
 #include "dm_kernels.h"
+#include "dm_ptx.cuh"
 
 namespace dmk {
 
 constexpr int kDftN = 256;
 constexpr int kDftRows = 16;     // rows per CTA tile
 constexpr int kTileElems = kDftRows * kDftN;
-constexpr size_t kDftSmem = 2 * kTileElems * sizeof(float2);   // two tiles (dynamic shared memory)
+constexpr int kZsPad = kDftRows + 1;   // FP32 form's output tile row (float2): conflict-free transposed writes
+constexpr size_t kDftSmem = (size_t)(kTileElems + kDftN * kZsPad) * sizeof(float2);   // exchange tile + output tile
 
 // W256^m (m < 256) and the pass-1 table of the register FFT (twF, [k1][t]),
 // filled once per device from double-precision angles.
 __device__ float2 g_dft_w[kDftN];
 __device__ float2 g_dft_twf[kDftN];
-
-__global__ void k_dft_tables() {
-  const int m = threadIdx.x;   // 256 threads
-  double s, c;
-  sincospi(-2.0 * (double)m / kDftN, &s, &c);
-  g_dft_w[m] = make_float2((float)c, (float)s);
-  const int k1 = m / 16, t = m % 16;
-  sincospi(-2.0 * (double)((t * k1) % kDftN) / kDftN, &s, &c);
-  g_dft_twf[m] = make_float2((float)c, (float)s);
-}
 
 // bf16 x2 register from two floats (low half = first)
 __device__ __forceinline__ uint32_t pack_bf16(float lo_part, float hi_part) {
@@ -104,6 +96,49 @@ __device__ __forceinline__ void dft_frags(DftFrags& f, int lane) {
     }
 }
 
+// The split fragments of F for both directions, per lane, built once per
+// device (FP64 angles are slow on this GPU: built in every CTA they cost
+// more than the transform): g_dft_frag[inv][part][register][lane], parts in
+// DftFrags order.
+__device__ uint32_t g_dft_frag[2][6][4][32];
+
+__global__ void k_dft_tables() {
+  const int m = threadIdx.x;   // 256 threads
+  double s, c;
+  sincospi(-2.0 * (double)m / kDftN, &s, &c);
+  g_dft_w[m] = make_float2((float)c, (float)s);
+  const int k1 = m / 16, t = m % 16;
+  sincospi(-2.0 * (double)((t * k1) % kDftN) / kDftN, &s, &c);
+  g_dft_twf[m] = make_float2((float)c, (float)s);
+  if (m < 64) {
+    const int lane = m & 31, inv = m >> 5;
+    DftFrags f;
+    if (inv) dft_frags<true>(f, lane); else dft_frags<false>(f, lane);
+    for (int i = 0; i < 4; ++i) {
+      g_dft_frag[inv][0][i][lane] = f.rh[i];
+      g_dft_frag[inv][1][i][lane] = f.rl[i];
+      g_dft_frag[inv][2][i][lane] = f.ih[i];
+      g_dft_frag[inv][3][i][lane] = f.il[i];
+      g_dft_frag[inv][4][i][lane] = f.nih[i];
+      g_dft_frag[inv][5][i][lane] = f.nil[i];
+    }
+  }
+}
+
+template <bool INV>
+__device__ __forceinline__ void load_frags(DftFrags& f, int lane) {
+  const int d = INV ? 1 : 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    f.rh[i] = g_dft_frag[d][0][i][lane];
+    f.rl[i] = g_dft_frag[d][1][i][lane];
+    f.ih[i] = g_dft_frag[d][2][i][lane];
+    f.il[i] = g_dft_frag[d][3][i][lane];
+    f.nih[i] = g_dft_frag[d][4][i][lane];
+    f.nil[i] = g_dft_frag[d][5][i][lane];
+  }
+}
+
 // One complex 16-point DFT of 8 lines: B fragments (real/imag, hi/lo) in,
 // FP32 accumulators (real/imag) out, 12 tensor-core products.
 __device__ __forceinline__ void dft16_tc(const DftFrags& f, const uint32_t (&xr)[2][2], const uint32_t (&xi)[2][2],
@@ -124,70 +159,124 @@ __device__ __forceinline__ void dft16_tc(const DftFrags& f, const uint32_t (&xr)
   mma_bf16(yi, f.rl, xi[0][0], xi[0][1]);
 }
 
-// B fragments of 8 lines from shared memory: element (k, n) at src(k, n).
-template <class Src>
-__device__ __forceinline__ void load_b(Src src, int lane, uint32_t (&xr)[2][2], uint32_t (&xi)[2][2]) {
-  const int n = lane >> 2, q = lane & 3;
-  for (int j = 0; j < 2; ++j) {
-    const float2 v0 = src(2 * q + 8 * j, n), v1 = src(2 * q + 8 * j + 1, n);
-    split2(v0.x, v1.x, xr[0][j], xr[1][j]);
-    split2(v0.y, v1.y, xi[0][j], xi[1][j]);
-  }
+// Operand planes of the tensor form.  Both stages multiply F by 256 lines of
+// 16 values each (stage A: line (r, t) holds x[r][t + 16 n2] over n2; stage
+// B: line (r, k1) holds the twiddled stage-A output over t).  The values are
+// split once, when a stage's input is written, into four BF16 planes (real
+// hi, real lo, imaginary hi, imaginary lo); a line is 32 bytes of a plane
+// (two 16-byte chunks: k = 0..7 and k = 8..15), and chunk c of line L sits at
+// chunk 2 L + (c ^ ((L >> 2) & 1)), so that the eight lines one ldmatrix
+// phase reads cover all 32 banks.  ldmatrix then hands each lane its B
+// fragments directly (lane g*4 + q: line g, k = 2q, 2q+1 and 2q+8, 2q+9).
+constexpr int kPlaneWords = 256 * 8;              // 32-bit words of one plane (256 lines x 32 bytes)
+constexpr int kZsRow = 321;                       // output tile row stride (float2), odd: conflict-free reads
+constexpr int kZsK2 = 20;                         // output tile stride of k2 (float2)
+constexpr size_t kDftTcSmem = 128 + (size_t)kTileElems * sizeof(float2) + 4 * kPlaneWords * sizeof(uint32_t) +
+                              (size_t)kDftRows * kZsRow * sizeof(float2);
+
+__device__ __forceinline__ int plane_word(int line, int w) {   // w: word (two k values), 0..7
+  return line * 8 + ((((w >> 2) ^ (line >> 2)) & 1) << 2) + (w & 3);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+// B fragments (hi and lo, real and imaginary) of lines L0 .. L0 + 7: two
+// ldmatrix.x4, each lane supplying one row address (lane = 8 * matrix + row;
+// matrices: hi chunk 0, hi chunk 1, lo chunk 0, lo chunk 1).
+__device__ __forceinline__ void load_b_planes(const uint32_t* planes, int L0, int lane, uint32_t (&xr)[2][2],
+                                              uint32_t (&xi)[2][2]) {
+  const int mi = lane >> 3, line = L0 + (lane & 7);
+  const int word = plane_word(line, (mi & 1) * 4);
+  const uint32_t re = smem_u32(planes + (mi >> 1) * kPlaneWords + word);
+  const uint32_t im = smem_u32(planes + (2 + (mi >> 1)) * kPlaneWords + word);
+  ldsm_x4(re, xr[0][0], xr[0][1], xr[1][0], xr[1][1]);
+  ldsm_x4(im, xi[0][0], xi[0][1], xi[1][0], xi[1][1]);
+}
+
+// Two consecutive values of a line (k, k + 1) into the four planes.
+__device__ __forceinline__ void store_planes(uint32_t* planes, int line, int w, float2 a, float2 b) {
+  uint32_t rh, rl, ih, il;
+  split2(a.x, b.x, rh, rl);
+  split2(a.y, b.y, ih, il);
+  const int o = plane_word(line, w);
+  planes[o] = rh;
+  planes[kPlaneWords + o] = rl;
+  planes[2 * kPlaneWords + o] = ih;
+  planes[3 * kPlaneWords + o] = il;
 }
 
 // Tensor-core row pass: 16 rows of frame `f` of `in` -> the same 16 columns of
 // frame f of `out` (out[f][k][r0 + r] = DFT(in[f][r0 + r])[k]).
 template <bool INV>
-__global__ void __launch_bounds__(kThreads) k_dft256_rows_tc(const float2* __restrict__ in, float2* __restrict__ out) {
-  extern __shared__ float2 dft_smem[];
-  float2* xs = dft_smem;                // input tile [r][x], then stage-A output [r][t][k1]
-  float2* zs = dft_smem + kTileElems;   // output tile [k][r]
+__global__ void __launch_bounds__(kThreads, 2) k_dft256_rows_tc(const float2* __restrict__ in,
+                                                                 float2* __restrict__ out) {
+  extern __shared__ unsigned char dft_raw[];
+  float2* xs = reinterpret_cast<float2*>(dft_raw + ((128u - (smem_u32(dft_raw) & 127u)) & 127u));   // input tile [r][x]
+  uint32_t* planes = reinterpret_cast<uint32_t*>(xs + kTileElems);                                 // 4 operand planes
+  float2* zs = reinterpret_cast<float2*>(planes + 4 * kPlaneWords);                                 // output [r][k2 * 20 + k1]
   const float2* tw256 = g_dft_w;
   const int f = blockIdx.x / (kDftN / kDftRows), r0 = (blockIdx.x % (kDftN / kDftRows)) * kDftRows;
   const float2* src = in + ((size_t)f * kDftN + r0) * kDftN;
   for (int i = threadIdx.x; i < kTileElems; i += kThreads) xs[i] = src[i];
   DftFrags fr;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  dft_frags<INV>(fr, lane);
+  load_frags<INV>(fr, lane);
+  __syncthreads();
+  // stage-A planes: line r * 16 + t, k = n2 (pairs n2 = 2w, 2w + 1)
+  for (int p = threadIdx.x; p < kTileElems / 2; p += kThreads) {
+    const int t = p & 15, w = (p >> 4) & 7, r = p >> 7;
+    const float2* row = xs + r * kDftN + t;
+    store_planes(planes, r * 16 + t, w, row[16 * (2 * w)], row[16 * (2 * w + 1)]);
+  }
   __syncthreads();
   const int g = lane >> 2, q = lane & 3;
   // stage A: lines (r, t), 32 groups of 8 (fixed r, t = t0 .. t0 + 7)
   float ya_r[4][4], ya_i[4][4];
+#pragma unroll
   for (int gi = 0; gi < 4; ++gi) {
     const int lg = warp * 4 + gi, r = lg >> 1, t0 = (lg & 1) * 8;
     uint32_t xr[2][2], xi[2][2];
-    load_b([&](int k, int n) { return xs[r * kDftN + t0 + n + 16 * k]; }, lane, xr, xi);
+    load_b_planes(planes, r * 16 + t0, lane, xr, xi);
     dft16_tc(fr, xr, xi, ya_r[gi], ya_i[gi]);
   }
-  __syncthreads();   // every stage-A input is read: xs takes the stage-A output
+  __syncthreads();   // every stage-A operand is read: the planes take the stage-B operands
+#pragma unroll
   for (int gi = 0; gi < 4; ++gi) {
     const int lg = warp * 4 + gi, r = lg >> 1, t0 = (lg & 1) * 8;
-    // accumulator (row k1 = g or g + 8, line n = 2q or 2q + 1)
-    for (int e = 0; e < 4; ++e) {
-      const int k1 = g + ((e >> 1) << 3), t = t0 + 2 * q + (e & 1);
-      const float2 w = tw256[(t * k1) & 255];
-      const float2 y = make_float2(ya_r[gi][e], ya_i[gi][e]);
-      xs[r * kDftN + t * 16 + k1] = ctw<INV>(y, w);
+    // accumulator e: row k1 = g (e < 2) or g + 8, line t = t0 + 2q + (e & 1)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k1 = g + 8 * h, ta = t0 + 2 * q;
+      const float2 ya = ctw<INV>(make_float2(ya_r[gi][2 * h], ya_i[gi][2 * h]), tw256[(ta * k1) & 255]);
+      const float2 yb = ctw<INV>(make_float2(ya_r[gi][2 * h + 1], ya_i[gi][2 * h + 1]), tw256[((ta + 1) * k1) & 255]);
+      // stage-B line r * 16 + k1, k = t (word t / 2)
+      store_planes(planes, r * 16 + k1, ta >> 1, ya, yb);
     }
   }
   __syncthreads();
   // stage B: lines (r, k1), 32 groups of 8 (fixed r, k1 = k10 .. k10 + 7)
+#pragma unroll
   for (int gi = 0; gi < 4; ++gi) {
     const int lg = warp * 4 + gi, r = lg >> 1, k10 = (lg & 1) * 8;
     uint32_t xr[2][2], xi[2][2];
-    load_b([&](int k, int n) { return xs[r * kDftN + k * 16 + k10 + n]; }, lane, xr, xi);
+    load_b_planes(planes, r * 16 + k10, lane, xr, xi);
     float yr[4], yi[4];
     dft16_tc(fr, xr, xi, yr, yi);
+#pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int k2 = g + ((e >> 1) << 3), k1 = k10 + 2 * q + (e & 1);
-      zs[(k1 + 16 * k2) * kDftRows + r] = make_float2(yr[e], yi[e]);
+      zs[r * kZsRow + k2 * kZsK2 + k1] = make_float2(yr[e], yi[e]);
     }
   }
   __syncthreads();
   float2* dst = out + (size_t)f * kDftN * kDftN + r0;
   for (int i = threadIdx.x; i < kTileElems; i += kThreads) {
     const int k = i / kDftRows, r = i % kDftRows;
-    dst[(size_t)k * kDftN + r] = zs[i];
+    dst[(size_t)k * kDftN + r] = zs[r * kZsRow + (k >> 4) * kZsK2 + (k & 15)];
   }
 }
 
@@ -198,7 +287,7 @@ __global__ void __launch_bounds__(kThreads) k_dft256_rows_fp32(const float2* __r
   constexpr int R1 = FftShape<kDftN>::R1, R2 = FftShape<kDftN>::R2;
   extern __shared__ float2 dft_smem[];
   float2* xs = dft_smem;                // exchange buffers [row][N]
-  float2* zs = dft_smem + kTileElems;   // output tile [k][r]
+  float2* zs = dft_smem + kTileElems;   // output tile [k][r], rows of kZsPad
   __shared__ float2 tw[kDftN];
   const int f = blockIdx.x / (kDftN / kDftRows), r0 = (blockIdx.x % (kDftN / kDftRows)) * kDftRows;
   for (int i = threadIdx.x; i < kDftN; i += kThreads) tw[i] = g_dft_twf[i];
@@ -213,12 +302,12 @@ __global__ void __launch_bounds__(kThreads) k_dft256_rows_fp32(const float2* __r
   __syncwarp();
   for (int tt = 0; tt < R2; ++tt) v[tt] = xg[t * R2 + (tt ^ t)];
   fft_pass2<kDftN, INV>(v);
-  for (int k2 = 0; k2 < R2; ++k2) zs[(t + R1 * k2) * kDftRows + gr] = v[p2_index<kDftN>(0, k2)];
+  for (int k2 = 0; k2 < R2; ++k2) zs[(t + R1 * k2) * kZsPad + gr] = v[p2_index<kDftN>(0, k2)];
   __syncthreads();
   float2* dst = out + (size_t)f * kDftN * kDftN + r0;
   for (int i = threadIdx.x; i < kTileElems; i += kThreads) {
     const int k = i / kDftRows, r = i % kDftRows;
-    dst[(size_t)k * kDftN + r] = zs[i];
+    dst[(size_t)k * kDftN + r] = zs[k * kZsPad + r];
   }
 }
 
@@ -227,8 +316,9 @@ __global__ void __launch_bounds__(kThreads) k_dft256_rows_fp32(const float2* __r
 cudaError_t prepare_dft256(cudaStream_t s) {
   const void* fs[4] = {(const void*)k_dft256_rows_tc<false>, (const void*)k_dft256_rows_tc<true>,
                        (const void*)k_dft256_rows_fp32<false>, (const void*)k_dft256_rows_fp32<true>};
-  for (const void* f : fs) {
-    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDftSmem);
+  for (int i = 0; i < 4; ++i) {
+    const cudaError_t e = cudaFuncSetAttribute(fs[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(i < 2 ? kDftTcSmem : kDftSmem));
     if (e != cudaSuccess) return e;
   }
   k_dft_tables<<<1, kDftN, 0, s>>>();
@@ -242,8 +332,8 @@ cudaError_t launch_dft256(const float2* in, float2* work, float2* out, int frame
     const float2* a = pass == 0 ? in : work;
     float2* b = pass == 0 ? work : out;
     if (precision == 1) {
-      if (inverse) k_dft256_rows_tc<true><<<blocks, kThreads, kDftSmem, s>>>(a, b);
-      else k_dft256_rows_tc<false><<<blocks, kThreads, kDftSmem, s>>>(a, b);
+      if (inverse) k_dft256_rows_tc<true><<<blocks, kThreads, kDftTcSmem, s>>>(a, b);
+      else k_dft256_rows_tc<false><<<blocks, kThreads, kDftTcSmem, s>>>(a, b);
     } else {
       if (inverse) k_dft256_rows_fp32<true><<<blocks, kThreads, kDftSmem, s>>>(a, b);
       else k_dft256_rows_fp32<false><<<blocks, kThreads, kDftSmem, s>>>(a, b);
