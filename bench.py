@@ -69,6 +69,9 @@ def parse():
                     help="--impl reference: views per worker process in each step's sample")
     ap.add_argument("--tte-iters", type=int, default=3000, help="tte: iteration limit of each DM run")
     ap.add_argument("--batch-iters", type=int, default=200, help="batch16: iterations of the convergence comparison")
+    ap.add_argument("--judge-iters", type=int, default=50,
+                    help="warmstart/tte: trial DM iterations from each start before the judge compares their "
+                         "Fourier errors (after 10 the learned start led, but stalled later)")
     ap.add_argument("--tte-psi-switch", type=float, default=5e-5,
                     help="tte: Eq. 6 object change below which the mixed form returns to complex64 exit waves")
     ap.add_argument("--tte-train-steps", type=int, default=3000, help="tte: training steps of the warm-start "
@@ -626,7 +629,7 @@ def run_warmstart(args, rank, local):
     kernels) on 50,000 DM-refined frames, measure its fit on the frames of two
     fresh scans, stitch its start for a 4-mode 128x128 scan (12x12 views,
     noise-free) and run DM from it and from the flat start; DM's Fourier
-    error after 10 trial iterations picks the start."""
+    error after --judge-iters trial iterations picks the start."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -640,7 +643,7 @@ def run_warmstart(args, rank, local):
                photons=ws.PHOTONS, seed=13)
     scan = make_scan(cfg, noise=False)
     o_warm = warmstart.predict_start(net, scan.intensities, scan.pos, scan.obj_shape)
-    _, pick, ef = warmstart.judged_start(scan, scan.probe, o_warm, trial_iters=10)
+    _, pick, ef = warmstart.judged_start(scan, scan.probe, o_warm, trial_iters=args.judge_iters)
     res = warmstart.compare(scan, scan.probe, o_warm, iters=200)
     levels = (0.2, 0.1, 0.05, 0.02, 0.01, 1e-3)
     runs = {name: {"start_error": r["errors"][0][1], "final_error": r["errors"][-1][1], "wall_s": r["wall_s"],
@@ -657,7 +660,8 @@ def run_warmstart(args, rank, local):
                                    f"{steps} Adam steps of 64 on 50,000 DM-refined frames; judged on a noise-free "
                                    "4-mode 128x128 scan, 12x12 views at 10 px, 250x250 object",
                        "params": nparams},
-            "training": training, "judge": {"pick": pick, "fourier_error_after_trial": ef}, "runs": runs,
+            "training": training, "judge": {"pick": pick, "trial_iterations": args.judge_iters,
+                                            "fourier_error_after_trial": ef}, "runs": runs,
         }), flush=True)
 
 
@@ -742,7 +746,7 @@ def run_tte(args, rank, local):
     would be fixed only up to that ramp.  Starts: a random object (white
     amplitude in [0.5, 1] and phase in [-pi/2, pi/2], three seeds), the flat
     object, and the judged warm start (the network trained here, stitched,
-    with DM's Fourier error after 10 trial iterations choosing between it and
+    with DM's Fourier error after --judge-iters trial iterations choosing between it and
     the flat start).  Runs: FP32 from each start, the mixed form from the
     random starts and the judged start.  Device seconds are CUDA-event time of the
     iterations (for the mixed form including its per-iteration check of the
@@ -775,13 +779,14 @@ def run_tte(args, rank, local):
         t_train = training["data_s"] + training["train_s"]
         t0 = time.perf_counter()
         o_warm = warmstart.predict_start(net, scan.intensities, scan.pos, scan.obj_shape)
-        chosen, pick, ef = warmstart.judged_start(scan, scan.probe, o_warm, trial_iters=10)
+        chosen, pick, ef = warmstart.judged_start(scan, scan.probe, o_warm, trial_iters=args.judge_iters)
         t_pick = time.perf_counter() - t0
         dm.dm_net_free(net)
         starts["judged"] = chosen
         train_info = {"steps": args.tte_train_steps, "train_s": t_train, "training": training,
                       "predict_and_judge_s": t_pick,
-                      "judge_pick": pick, "fourier_error_after_trial": ef,
+                      "judge_pick": pick, "judge_trial_iterations": args.judge_iters,
+                      "fourier_error_after_trial": ef,
                       "predicted_start_error": ws.object_error(o_warm.detach().cpu().numpy(), scan.obj, covered)}
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
