@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--autotune", type=int, default=0, metavar="V",
                     help="pick the Fourier-step plan with dm_autotune on the first V views before timing (0: the "
                          "default plan)")
+    ap.add_argument("--form", choices=["auto", "strip", "split"], default="auto",
+                    help="Fourier-step form (auto: the context's choice, the split form for 256x256 frames with 8 "
+                         "modes; after --autotune the autotuner's)")
     ap.add_argument("--psi", choices=["fp32", "fp16"], default="fp32",
                     help="exit-wave storage of the timed iteration (fp16: the mixed-precision form, no switch)")
     ap.add_argument("--cpu-views", type=int, default=600, help="views in the one-process oracle sample")
@@ -188,27 +191,31 @@ def make_inputs(views, device, name=WORKLOAD):
     return s, p0.astype(np.complex64), o0.astype(np.complex64)
 
 
-def kernel_source_hash():
-    """Hash of the Fourier-step kernel sources; a stored DRAM-traffic figure
-    is used only while it matches."""
+FORM_KERNEL = {"strip": "dm_fourier.cu", "split": "dm_fourier_split.cu"}
+FORM_TRAFFIC = {"strip": "fourier_mm256_traffic.json", "split": "fourier_split_mm256_traffic.json"}
+
+
+def kernel_source_hash(form="strip"):
+    """Hash of the sources of one form of the Fourier-step kernel; a stored
+    DRAM-traffic figure is used only while it matches."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("dm_fourier.cu", "dm_fft.cuh", "dm_kernels.h", "dm_psi.cuh", "dm_ptx.cuh"):
+    for f in (FORM_KERNEL[form], "dm_fft.cuh", "dm_kernels.h", "dm_psi.cuh", "dm_ptx.cuh"):
         with open(os.path.join(ROOT, "paper_1808_10375_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def stored_traffic(views):
-    """DRAM bytes of one Fourier-step launch from the committed ncu summary,
-    scaled from its capture size to `views` views, or None if the kernel
-    changed since the capture."""
+def stored_traffic(views, form="strip"):
+    """DRAM bytes of one Fourier-step launch of the given form from the
+    committed ncu summary, scaled from its capture size to `views` views, or
+    None if the kernel changed since the capture."""
     try:
-        with open(os.path.join(ROOT, "profiles", "fourier_mm256_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", FORM_TRAFFIC[form])) as f:
             d = json.load(f)
     except Exception:
         return None
-    if d.get("source_hash") != kernel_source_hash():
+    if d.get("source_hash") != kernel_source_hash(form):
         return None
     return d["dram_bytes_per_launch"] * views / d["views"]
 
@@ -920,8 +927,12 @@ def main():
     torch.cuda.set_stream(stream)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     ctx = dm.dm_init(params, dev(s.pos), s.intensities, dev(p0), dev(o0), stream=stream.cuda_stream)
+    form_req = {"strip": dm.DM_FOURIER_STRIP, "split": dm.DM_FOURIER_SPLIT}.get(args.form)
+    if form_req is not None:
+        dm.dm_set_fourier_form(ctx, form_req)
     if args.autotune > 0:
         dm.dm_autotune(ctx, sample_views=min(j, args.autotune))
+    form = "split" if dm.dm_get_fourier_form(ctx) == dm.DM_FOURIER_SPLIT else "strip"
     plan = dm.dm_get_plan(ctx)
     dm.dm_iterate(ctx, args.warmup)
     dm.dm_sync(ctx)
@@ -956,8 +967,10 @@ def main():
     fft_tflops = fourier_flops_per_view(n, m) * j / launch_s / 1e12 if f_n else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None,
-                "traffic": stored_traffic(j) if wname == WORKLOAD else None,
-                "kernel": "k_fourier (persistent Fourier step, Eq. 3)", "peak_kind": peak_kind,
+                "traffic": stored_traffic(j, form) if (wname == WORKLOAD and args.psi == "fp32") else None,
+                "kernel": ("k_fourier_split (persistent Fourier step, Eq. 3, split-column form)" if form == "split"
+                           else "k_fourier (persistent Fourier step, Eq. 3, strip form)"),
+                "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": f_bytes, "avg_launch_ms": f_ms / f_n if f_n else None,
                 "object_source_bytes_per_launch": c_bytes,
                 "frac_with_object_source": ((f_bytes + c_bytes) / launch_s / 1e9 / hbm) if f_n else None,
@@ -985,6 +998,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         c2 = dm.dm_init(params, pos_h, inten_h, p0_h, o0_h, stream=stream.cuda_stream)
+        if form_req is not None:
+            dm.dm_set_fourier_form(c2, form_req)
         dm.dm_iterate(c2, args.steps)
         dm.dm_get_object(c2, out=o_out)
         dm.dm_get_probe(c2, out=p_out)
@@ -1017,6 +1032,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (exit waves %.1f GB)" % (j * m * n * n * 8 / 1e9),
                        "fourier_plan": dict(plan, autotuned=args.autotune > 0),
+                       "fourier_form": form,
                        "iteration_algorithmic_bytes": iter_bytes,
                        "iteration_hbm_frac": iter_bytes / (t_ms / args.steps / 1e3) / 1e9 / hbm},
             "roofline": roofline,

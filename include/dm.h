@@ -263,7 +263,10 @@ int dm_set_graph(dm_ctx* ctx, int32_t enable);
  * of scratch-ring size (48, 64, 96, 128 MiB), column-task size (64, 128,
  * 256 KiB of scratch) and strip buffers (2, 3) is timed on the first
  * sample_views views of the context (one warm-up and three timed runs of the
- * Fourier kernel each); the fastest is kept for the whole scan.  The exit
+ * Fourier kernel each); where the scan has the split form (and the exit-wave
+ * change is not tracked), that form is timed too at each ring size, so the
+ * choice covers the form as well (dm_get_fourier_form reports it).  The
+ * fastest is kept for the whole scan.  The exit
  * waves of the sample views are restored afterwards; the object sources are
  * recomputed by the next iteration, so results are unchanged.  Temporary
  * buffers (up to the largest ring plus a copy of the sample's exit waves)
@@ -273,8 +276,32 @@ int dm_set_graph(dm_ctx* ctx, int32_t enable);
 int dm_autotune(dm_ctx* ctx, int32_t sample_views, double* best_ms);
 
 /* The current Fourier-step plan: out[0] scratch-ring bytes, out[1] views per
- * chunk, out[2] strips per column task, out[3] strip buffers, out[4] CTAs. */
+ * chunk, out[2] strips per column task, out[3] strip buffers, out[4] CTAs.
+ * For the split form out[2] is 0 and out[3] the item buffers of each of a
+ * column task's two item lanes. */
 int dm_get_plan(const dm_ctx* ctx, int64_t* out);
+
+/* Two forms of the Fourier step (Eq. 3 with the constrained transform F_c of
+ * Sec. II); both compute the same iteration to FP32 rounding.
+ * DM_FOURIER_STRIP: row tasks take the row DFTs, column tasks the column
+ * DFTs, the modulus projection and the inverse column DFTs of 2-column
+ * strips of all modes; every frame size, mode count and exit-wave storage.
+ * DM_FOURIER_SPLIT (256 x 256 frames with exactly 8 modes): the 256-point
+ * column DFT is split into two radix-16 stages, the first in the row tasks
+ * (over rows n1 + 16 n2 of one residue n1) and the second in the column
+ * tasks, whose work items are 16 columns x 16 rows x 8 modes; the mode sum
+ * of F_c is then a warp-shuffle reduction.  It keeps the intensities in a
+ * second layout as well (4 N^2 bytes more per view).  The exit-wave change
+ * (dm_set_psi_error) and dm_batch iterations run the strip form.  Contexts
+ * start in the strip form; dm_autotune times both where both exist and keeps
+ * the faster, and dm_set_fourier_form selects one explicitly
+ * (DM_EINVAL for DM_FOURIER_SPLIT on other shapes); it synchronises and
+ * drops captured iteration graphs.  dm_get_fourier_form
+ * reports the form the next Fourier step runs. */
+#define DM_FOURIER_STRIP 0
+#define DM_FOURIER_SPLIT 1
+int dm_set_fourier_form(dm_ctx* ctx, int32_t form);
+int dm_get_fourier_form(const dm_ctx* ctx, int32_t* form);
 
 /* Several scans advanced together (the batched form).  The contexts (same
  * device; any frame sizes, mode and view counts) keep their own data and

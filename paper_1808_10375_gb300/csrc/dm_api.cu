@@ -101,6 +101,16 @@ struct dm_ctx {
   int tiles_x = 0, tiles_y = 0, obj_final_blocks = 0;
   CUtensorMap tmap_c;
   CUtensorMap tmap_s[2];   // scratch ring: box of all modes, box of one mode
+  // the split-column form of the Fourier step (256 x 256 frames, 8 modes)
+  bool split_ok = false;        // the form exists for this scan
+  int form = DM_FOURIER_STRIP;  // the form dm_iterate runs
+  float* isplit = nullptr;      // intensities in the split layout
+  dmk::FourierArgs fs{};        // its plan (shares the scratch ring and counters of fa)
+  int* stage_off_s = nullptr;
+  int fsgrid = 0;
+  size_t fssmem = 0;
+  CUtensorMap tmap_split[2];    // scratch rows (box 16 x 128, swizzled), intensities (box 16 x 16)
+  int ef_cg = 0;                // column tasks per view of the last Fourier launch (rows of ef_part)
   int probe_groups = 0;
   int probe_final_blocks = 0;
   int64_t iters = 0;
@@ -270,7 +280,7 @@ FourierKnobs default_knobs(const dm_ctx* c) {
 // (stage offsets), the scratch ring, the strip buffers and the launch shape.
 // Fills everything in `a` but the device pointers.
 int fourier_schedule(dm_ctx* c, int J, const FourierKnobs& k, dmk::FourierArgs& a, std::vector<int>& off,
-                     size_t& smem, int& grid) {
+                     size_t& smem, int& grid, bool split = false) {
   const int N = c->N, M = c->M;
   const int R2 = dmk::fourier_r2(N);
   const int groups = dmk::kThreads / R2;
@@ -297,6 +307,13 @@ int fourier_schedule(dm_ctx* c, int J, const FourierKnobs& k, dmk::FourierArgs& 
   a.strip_bufs =
       2 * a.G * (strip_bytes + (size_t)N * a.w * sizeof(float)) <= kColumnSmemBudget ? k.max_bufs : 1;
   a.strip_bufs = std::max(1, std::min(a.strip_bufs, dmk::kMaxStripBufs));
+  if (split) {
+    a.RB = dmk::kSplitN / 16;
+    a.CG = dmk::kSplitN / 16;
+    a.SPG = 0;
+    a.G = 1;
+    a.strip_bufs = 0;
+  }
   a.lag = kFourierLag;
   a.nslot = 2 * a.lag + 2;
   const size_t view_bytes = (size_t)M * N * N * sizeof(float2);
@@ -318,6 +335,15 @@ int fourier_schedule(dm_ctx* c, int J, const FourierKnobs& k, dmk::FourierArgs& 
   if (total >= (1ll << 31)) return fail(c, DM_EINVAL, "too many Fourier tasks");
   a.total_tasks = (int)total;
   a.beta = c->p.beta;
+  if (split) {
+    // the split form: 16 row tasks (one per row residue n1), 16 column tasks
+    // (one per k1) and 16 inverse row tasks per view; no strips
+    smem = dmk::fourier_split_smem_bytes();
+    const int occ = dmk::fourier_split_occupancy(smem);
+    if (occ < 1) return fail(c, DM_ECUDA, "split Fourier kernel does not fit on an SM");
+    grid = std::max(1, std::min(a.total_tasks, occ * c->num_sms));
+    return DM_OK;
+  }
   // an extra strip buffer is only worth it while it costs no resident CTA
   while (a.strip_bufs > 1 &&
          dmk::fourier_occupancy(N, dmk::fourier_smem_bytes(N, M, a.strip_bufs, a.G)) <
@@ -358,6 +384,45 @@ int encode_scratch_map(dm_ctx* c, const dmk::FourierArgs& a, float2* scratch, CU
 
 size_t scratch_elems(const dmk::FourierArgs& a) { return (size_t)a.nslot * a.B * a.M * a.N * a.N; }
 
+// TMA views of the split form: the scratch ring as rows of N complex values
+// (one row per (view, k1, n1, mode)), box 16 columns x 16 M rows with the
+// 128-byte swizzle; the split-layout intensities as rows of 16 floats (one
+// row per (view, k1, column)), box 16 x 16.
+int encode_split_maps(dm_ctx* c, const dmk::FourierArgs& a, float2* scratch, CUtensorMap* map) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  DM_CUDA(c, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+  if (!fn || q != cudaDriverEntryPointSuccess) return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const int N = a.N, M = a.M;
+  const cuuint32_t estr[2] = {1, 1};
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)a.nslot * a.B * 16 * 16 * M};
+    const cuuint64_t strides[1] = {(cuuint64_t)N * sizeof(float2)};
+    const cuuint32_t box[2] = {16, (cuuint32_t)(16 * M)};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, scratch, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled (split scratch) failed (" + std::to_string((int)r) + ")");
+  }
+  {
+    const cuuint64_t dims[2] = {16, (cuuint64_t)c->J * 16 * N};
+    const cuuint64_t strides[1] = {16 * sizeof(float)};
+    const cuuint32_t box[2] = {16, 16};
+    const CUresult r = encode(map + 1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->isplit, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(c, DM_ECUDA, "cuTensorMapEncodeTiled (split intensities) failed (" + std::to_string((int)r) + ")");
+  }
+  return DM_OK;
+}
+
+// Whether the next Fourier step runs the split form (the exit-wave change is
+// tracked by the strip form only).
+bool use_split(const dm_ctx* c) { return c->split_ok && c->form == DM_FOURIER_SPLIT && !c->psi_err; }
+
 // Plan the Fourier step of the whole scan with knobs `k` and allocate its
 // buffers (scratch ring, stage offsets, counters, Fourier-error partials).
 int plan_fourier(dm_ctx* c, const FourierKnobs& k) {
@@ -367,13 +432,31 @@ int plan_fourier(dm_ctx* c, const FourierKnobs& k) {
   if ((rc = fourier_schedule(c, c->J, k, a, off, c->fsmem, c->fgrid))) return rc;
   if ((rc = alloc_n(c, &c->scratch, scratch_elems(a)))) return rc;
   if ((rc = alloc_n(c, &c->stage_off, off.size()))) return rc;
-  c->counters_bytes = sizeof(int) * (1 + 3 * (size_t)a.nchunks);
+  // the single-scan kernels count completed tasks per view, the batched one
+  // per chunk (at most one per view)
+  c->counters_bytes = sizeof(int) * (1 + 3 * (size_t)c->J);
   if ((rc = dev_alloc(c, reinterpret_cast<void**>(&c->counters), c->counters_bytes))) return rc;
-  if ((rc = alloc_n(c, &c->ef_part, (size_t)c->J * a.CG))) return rc;
+  if ((rc = alloc_n(c, &c->ef_part, (size_t)c->J * std::max(a.CG, dmk::kSplitN / 16)))) return rc;
   DM_CUDA(c, cudaMemcpyAsync(c->stage_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice,
                              c->stream));
   DM_CUDA(c, cudaStreamSynchronize(c->stream));  // `off` is a host temporary
   if ((rc = encode_scratch_map(c, a, c->scratch, c->tmap_s))) return rc;
+  if (c->split_ok) {
+    // the split form with the same ring (same views per chunk and slots)
+    dmk::FourierArgs& s = c->fs;
+    std::vector<int> soff;
+    if ((rc = fourier_schedule(c, c->J, k, s, soff, c->fssmem, c->fsgrid, true))) return rc;
+    if ((rc = alloc_n(c, &c->stage_off_s, soff.size()))) return rc;
+    DM_CUDA(c, cudaMemcpyAsync(c->stage_off_s, soff.data(), soff.size() * sizeof(int), cudaMemcpyHostToDevice,
+                               c->stream));
+    DM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if ((rc = encode_split_maps(c, s, c->scratch, c->tmap_split))) return rc;
+    s.psi = psi_cur(c); s.psi16 = c->half ? 1 : 0;
+    s.istrip = c->isplit; s.pos = c->pos; s.cview = c->cview;
+    s.scratch = c->scratch; s.ef_part = c->ef_part; s.tw = c->tw;
+    s.stage_off = c->stage_off_s; s.counters = c->counters; s.status = c->status;
+    s.psi_part = nullptr;
+  }
   a.psi = psi_cur(c); a.psi16 = c->half ? 1 : 0;
   a.istrip = c->istrip; a.pos = c->pos; a.cview = c->cview;
   a.scratch = c->scratch; a.ef_part = c->ef_part; a.tw = c->tw;
@@ -458,12 +541,16 @@ int plan_probe(dm_ctx* c) {
 
 int run_fourier(dm_ctx* c) {
   DM_CUDA(c, cudaMemsetAsync(c->counters, 0, c->counters_bytes, c->stream));
-  c->fa.probe = c->probe[c->cur_P];
-  c->fa.obj = c->obj[c->cur_O];
-  c->fa.psi = psi_cur(c);
-  c->fa.psi16 = c->half ? 1 : 0;
+  const bool split = use_split(c);
+  dmk::FourierArgs& a = split ? c->fs : c->fa;
+  a.probe = c->probe[c->cur_P];
+  a.obj = c->obj[c->cur_O];
+  a.psi = psi_cur(c);
+  a.psi16 = c->half ? 1 : 0;
+  c->ef_cg = a.CG;
   Timed t(c, DM_KERNEL_FOURIER);
-  DM_CUDA(c, dmk::launch_fourier(c->tmap_s, c->fa, c->fgrid, c->fsmem, c->stream));
+  if (split) DM_CUDA(c, dmk::launch_fourier_split(c->tmap_split, a, c->fsgrid, c->fssmem, c->stream));
+  else DM_CUDA(c, dmk::launch_fourier(c->tmap_s, a, c->fgrid, c->fsmem, c->stream));
   return DM_OK;
 }
 
@@ -669,6 +756,9 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   }
   DM_TRY(alloc_n(c, &c->cview, (size_t)J * nn));
   DM_TRY(alloc_n(c, &c->istrip, (size_t)J * nn));
+  c->split_ok = N == dmk::kSplitN && M == dmk::kSplitModes;
+  c->form = DM_FOURIER_STRIP;   // the faster form on the 10,000-view workload; dm_autotune may pick the other
+  if (c->split_ok) DM_TRY(alloc_n(c, &c->isplit, (size_t)J * nn));
   DM_TRY(alloc_n(c, &c->probe[0], (size_t)M * nn));
   DM_TRY(alloc_n(c, &c->probe[1], (size_t)M * nn));
   DM_TRY(alloc_n(c, &c->obj[0], (size_t)c->H * c->W));
@@ -716,6 +806,9 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   if ((e = dmk::launch_reduce_sum(isum_part, ib, 1, 0, c->isum, c->stream)) != cudaSuccess) {
     cuda_fail(c, e, "intensity sum"); return bail(DM_ECUDA);
   }
+  if (c->split_ok && (e = dmk::launch_intensity_split(c->isplit, dev_i, J, c->stream)) != cudaSuccess) {
+    cuda_fail(c, e, "split intensity layout"); return bail(DM_ECUDA);
+  }
   if ((e = dmk::launch_p2(c->p2, c->probe[0], N, M, c->stream)) != cudaSuccess) { cuda_fail(c, e, "p2"); return bail(DM_ECUDA); }
   if ((e = dmk::launch_init_psi(psi_cur(c), c->half ? 1 : 0, c->probe[0], c->obj[0], c->pos, N, M, J, c->W,
                                 c->stream)) != cudaSuccess) {
@@ -762,7 +855,7 @@ int enqueue_iteration(dm_ctx* c, bool upd) {
     if (!upd) break;  // later passes would repeat the same object update
     if ((rc = run_probe(c, probe_object(c)))) return rc;
   }
-  return run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd, true);
+  return run_metrics(c, c->ef_part, (long long)c->J * c->ef_cg, c->isum, upd, true);
 }
 
 // The iteration for the current (object, probe) buffers as an instantiated
@@ -878,24 +971,30 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
     std::vector<int> off;
     size_t smem;
     int grid;
+    bool split;
   };
   std::vector<Plan> plans;
   size_t max_scr = 0, max_off = 0, max_cnt = 0;
-  for (size_t mb : {48, 64, 96, 128})
-    for (size_t kb : {64, 128, 256})
-      for (int b : {2, 3}) {
-        Plan pl;
-        pl.k = FourierKnobs{mb << 20, kb << 10, b};
-        if ((rc = fourier_schedule(c, Js, pl.k, pl.a, pl.off, pl.smem, pl.grid))) return rc;
-        bool dup = false;
-        for (const Plan& q : plans)
-          dup = dup || (q.a.B == pl.a.B && q.a.SPG == pl.a.SPG && q.a.strip_bufs == pl.a.strip_bufs);
-        if (dup) continue;
-        max_scr = std::max(max_scr, scratch_elems(pl.a));
-        max_off = std::max(max_off, pl.off.size());
-        max_cnt = std::max(max_cnt, 1 + 3 * (size_t)pl.a.nchunks);
-        plans.push_back(std::move(pl));
-      }
+  // the split form (where the scan has it, and unless the exit-wave change
+  // is tracked) competes with the strip plans; its only knob is the ring
+  for (int split = 0; split <= (c->split_ok && !c->psi_err ? 1 : 0); ++split)
+    for (size_t mb : {48, 64, 96, 128})
+      for (size_t kb : {64, 128, 256})
+        for (int b : {2, 3}) {
+          Plan pl;
+          pl.k = FourierKnobs{mb << 20, kb << 10, b};
+          pl.split = split != 0;
+          if ((rc = fourier_schedule(c, Js, pl.k, pl.a, pl.off, pl.smem, pl.grid, pl.split))) return rc;
+          bool dup = false;
+          for (const Plan& q : plans)
+            dup = dup || (q.split == pl.split && q.a.B == pl.a.B && q.a.SPG == pl.a.SPG &&
+                          q.a.strip_bufs == pl.a.strip_bufs);
+          if (dup) continue;
+          max_scr = std::max(max_scr, scratch_elems(pl.a));
+          max_off = std::max(max_off, pl.off.size());
+          max_cnt = std::max(max_cnt, 1 + 3 * (size_t)Js);
+          plans.push_back(std::move(pl));
+        }
   float2 *scr = nullptr, *psi_save = nullptr;
   int *offd = nullptr, *cnt = nullptr;
   double* ef = nullptr;
@@ -916,30 +1015,37 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
   cudaEvent_t e0 = take_event(c), e1 = take_event(c);
   double best = 1e300;
   FourierKnobs best_k = c->knobs;
+  bool best_split = use_split(c);
   constexpr int kReps = 3;
   for (Plan& pl : plans) {
     dmk::FourierArgs a = pl.a;
     a.psi = psi_cur(c); a.psi16 = c->half ? 1 : 0;
-    a.istrip = c->istrip; a.pos = c->pos; a.cview = c->cview; a.scratch = scr; a.ef_part = ef;
+    a.istrip = pl.split ? c->isplit : c->istrip; a.pos = c->pos; a.cview = c->cview; a.scratch = scr; a.ef_part = ef;
     a.tw = c->tw; a.stage_off = offd; a.counters = cnt; a.status = c->status;
     a.probe = c->probe[c->cur_P]; a.obj = c->obj[c->cur_O];
     CUtensorMap map[2];
-    if ((rc = encode_scratch_map(c, a, scr, map))) { release(); return rc; }
+    if ((rc = pl.split ? encode_split_maps(c, a, scr, map) : encode_scratch_map(c, a, scr, map))) {
+      release();
+      return rc;
+    }
     cudaError_t e = cudaMemcpyAsync(offd, pl.off.data(), pl.off.size() * sizeof(int), cudaMemcpyHostToDevice,
                                     c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    dmk::fourier_occupancy(N, pl.smem);   // sets the kernel's shared-memory limit for this plan
+    // sets the kernel's shared-memory limit for this plan
+    if (pl.split) dmk::fourier_split_occupancy(pl.smem); else dmk::fourier_occupancy(N, pl.smem);
     for (int r = 0; r <= kReps && e == cudaSuccess; ++r) {   // the first run warms up
       if (r == 1) e = cudaEventRecord(e0, c->stream);
-      if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 3 * (size_t)a.nchunks), c->stream);
-      if (e == cudaSuccess) e = dmk::launch_fourier(map, a, pl.grid, pl.smem, c->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 3 * (size_t)Js), c->stream);
+      if (e == cudaSuccess)
+        e = pl.split ? dmk::launch_fourier_split(map, a, pl.grid, pl.smem, c->stream)
+                     : dmk::launch_fourier(map, a, pl.grid, pl.smem, c->stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e != cudaSuccess) { release(); return cuda_fail(c, e, "autotune run"); }
-    if (ms / kReps < best) { best = ms / kReps; best_k = pl.k; }
+    if (ms / kReps < best) { best = ms / kReps; best_k = pl.k; best_split = pl.split; }
   }
   c->event_pool.push_back(e0);
   c->event_pool.push_back(e1);
@@ -952,20 +1058,45 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
   for (auto& row : c->gexec)
     for (auto& g : row)
       if (g) { cudaGraphExecDestroy(g); g = nullptr; }
-  for (void* q : {(void*)c->scratch, (void*)c->stage_off, (void*)c->counters, (void*)c->ef_part}) dev_free(c, q);
-  c->scratch = nullptr; c->stage_off = nullptr; c->counters = nullptr; c->ef_part = nullptr;
+  for (void* q : {(void*)c->scratch, (void*)c->stage_off, (void*)c->counters, (void*)c->ef_part, (void*)c->stage_off_s})
+    dev_free(c, q);
+  c->scratch = nullptr; c->stage_off = nullptr; c->counters = nullptr; c->ef_part = nullptr; c->stage_off_s = nullptr;
   if ((rc = plan_fourier(c, best_k))) return rc;
+  if (c->split_ok) c->form = best_split ? DM_FOURIER_SPLIT : DM_FOURIER_STRIP;
   if (best_ms) *best_ms = best;
   return DM_OK;
 }
 
 int dm_get_plan(const dm_ctx* c, int64_t* out) {
   if (!c || !out) return DM_EINVAL;
+  const bool split = use_split(c);
   out[0] = (int64_t)scratch_elems(c->fa) * (int64_t)sizeof(float2);
   out[1] = c->fa.B;
-  out[2] = c->fa.SPG;
-  out[3] = c->fa.strip_bufs;
-  out[4] = c->fgrid;
+  out[2] = split ? 0 : c->fa.SPG;
+  out[3] = split ? dmk::kSplitBufs : c->fa.strip_bufs;
+  out[4] = split ? c->fsgrid : c->fgrid;
+  return DM_OK;
+}
+
+int dm_set_fourier_form(dm_ctx* c, int32_t form) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (form != DM_FOURIER_STRIP && form != DM_FOURIER_SPLIT) return fail(c, DM_EINVAL, "unknown Fourier form");
+  if (form == DM_FOURIER_SPLIT && !c->split_ok)
+    return fail(c, DM_EINVAL, "the split form needs 256 x 256 frames and 8 modes");
+  if (form == c->form) return DM_OK;
+  DM_CUDA(c, cudaStreamSynchronize(c->stream));   // no captured iteration is in flight below
+  c->form = form;
+  // captured iterations hold the previous Fourier-step instance
+  for (auto& row : c->gexec)
+    for (auto& g : row)
+      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  return DM_OK;
+}
+
+int dm_get_fourier_form(const dm_ctx* c, int32_t* form) {
+  if (!c || c->magic != 0x58434D44u || !form) return DM_EINVAL;
+  *form = use_split(c) ? DM_FOURIER_SPLIT : DM_FOURIER_STRIP;
   return DM_OK;
 }
 
@@ -1027,6 +1158,7 @@ int enqueue_batch_iteration(dm_batch* b) {
       c->fa.obj = c->obj[c->cur_O];
       fb.a[s] = c->fa;
       fb.map[s] = c->tmap_s[0];
+      c->ef_cg = c->fa.CG;   // the batched launch runs the strip form
       fb.base[s] = base;
       base += c->fa.total_tasks;
       DM_BCUDA(b, cudaMemsetAsync(c->counters, 0, c->counters_bytes, b->stream));
@@ -1295,7 +1427,7 @@ int dm_fourier_error_partials(dm_ctx* c, double* sums) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!sums) return fail(c, DM_EINVAL, "sums is NULL");
-  DM_CUDA(c, dmk::launch_reduce_sum(c->ef_part, (long long)c->J * c->fa.CG, 1, 0, c->ef_tot, c->stream));
+  DM_CUDA(c, dmk::launch_reduce_sum(c->ef_part, (long long)c->J * c->ef_cg, 1, 0, c->ef_tot, c->stream));
   DM_CUDA(c, cudaMemcpyAsync(c->ef_tot + 1, c->isum, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   if ((rc = copy_out(c, sums, c->ef_tot, 2 * sizeof(double), DM_HOST))) return rc;
   return check_status(c);

@@ -728,10 +728,12 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   Pipe pp = {};
 
+  // per-view completion counters: a column task waits for the row tasks of
+  // its own view only (and so on), not for the slowest task of its chunk
   int* disp = a.counters;
   int* doneR = a.counters + 1;
-  int* doneC = doneR + a.nchunks;
-  int* doneI = doneC + a.nchunks;
+  int* doneC = doneR + a.J;
+  int* doneI = doneC + a.J;
   int next = 0;
   if (threadIdx.x == 0) next = atomicAdd(disp, 1);
   int st_prev = 0;
@@ -776,19 +778,18 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
     if (kind < 0) { kind = 2; c = st - 2 * a.lag; }
+    const int jv = c * a.B + local / (kind == 1 ? a.CG : a.RB);   // the task's view
 
     // Wait for what this task consumes.
     if (threadIdx.x == 0) {
       bool ok = true;
       if (kind == 0) {
-        if (c >= a.nslot) {
-          const int cp = c - a.nslot;
-          ok = spin_wait_geq(doneI + cp, min(a.B, a.J - cp * a.B) * a.RB, a.status);
-        }
+        // the slot's area of this view was last used by view jv - nslot B
+        if (c >= a.nslot) ok = spin_wait_geq(doneI + (jv - a.nslot * a.B), a.RB, a.status);
       } else if (kind == 1) {
-        ok = spin_wait_geq(doneR + c, min(a.B, a.J - c * a.B) * a.RB, a.status);
+        ok = spin_wait_geq(doneR + jv, a.RB, a.status);
       } else {
-        ok = spin_wait_geq(doneC + c, min(a.B, a.J - c * a.B) * a.CG, a.status);
+        ok = spin_wait_geq(doneC + jv, a.CG, a.status);
       }
       s_skip = ok ? 0 : 1;
     }
@@ -845,7 +846,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (threadIdx.x == 0) {
       bulk_wait<0>();   // TMA stores of the task have landed
       __threadfence();
-      atomicAdd((kind == 0 ? doneR : kind == 1 ? doneC : doneI) + c, 1);
+      atomicAdd((kind == 0 ? doneR : kind == 1 ? doneC : doneI) + jv, 1);
     }
   }
   // Copies that a timed-out wait left in flight must land before the CTA exits.

@@ -64,9 +64,26 @@ struct FourierArgs {
                           // every slot): G * M slots busy out of kThreads / (w R2)
   int nstages, total_tasks;
   const int* stage_off;   // [nstages + 1] first task of each stage
-  int* counters;          // [0] dispenser, then done R/C/I per chunk
+  int* counters;          // [0] dispenser, then done R/C/I per view [J] (single-scan kernels)
+                          // or per chunk [nchunks] (the batched kernel)
   int* status;
 };
+
+// The split-column form of the Fourier step (dm_fourier_split.cu) for N x N
+// = 256 x 256 frames and 8 modes: the column DFT's first radix-16 stage runs
+// in the row tasks, its second in the column tasks, whose items are 16
+// columns x 16 rows x 8 modes (one TMA box of 128-byte rows).  Tasks per
+// view: RB = CG = 16.  tmaps: [0] the scratch ring as rows of N complex
+// values (box 16 x 128, 128-byte swizzle), [1] the intensities in the split
+// layout (launch_intensity_split) as rows of 16 floats (box 16 x 16).
+constexpr int kSplitN = 256;
+constexpr int kSplitModes = 8;
+constexpr int kSplitBufs = 3;          // item buffers per item lane of a column task
+cudaError_t launch_fourier_split(const void* tmaps, const FourierArgs& a, int grid, size_t smem, cudaStream_t s);
+size_t fourier_split_smem_bytes();
+int fourier_split_occupancy(size_t smem);
+// isplit[j][k1][x][k2] = inten[j][k1 + 16 k2][x] (J views of 256 x 256)
+cudaError_t launch_intensity_split(float* isplit, const float* inten, int J, cudaStream_t s);
 
 // Several scans of one frame size in one persistent Fourier launch: scan s
 // owns tasks [base[s], base[s+1]) of the launch counter; its own plan,

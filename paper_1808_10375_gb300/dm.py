@@ -26,6 +26,7 @@ DM_STEP_FOURIER, DM_STEP_OBJECT, DM_STEP_PROBE = 0, 1, 2
 DM_DFT_FP32, DM_DFT_BF16X3 = 0, 1
 DM_ORDER_GAUSS_SEIDEL, DM_ORDER_JACOBI = 0, 1
 DM_PSI_FP32, DM_PSI_FP16 = 0, 1
+DM_FOURIER_STRIP, DM_FOURIER_SPLIT = 0, 1
 DM_NET_LOSS_MSE, DM_NET_LOSS_GAUGE = 0, 1
 (DM_KERNEL_FOURIER, DM_KERNEL_OBJECT_GATHER, DM_KERNEL_OBJECT_FINAL, DM_KERNEL_PROBE_PARTIAL,
  DM_KERNEL_PROBE_FINAL, DM_KERNEL_METRICS, DM_KERNEL_OTHER, DM_KERNEL_COUNT) = range(8)
@@ -63,7 +64,7 @@ EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_
            "dm_object_partials", "dm_object_apply", "dm_probe_partials", "dm_probe_apply",
            "dm_fourier_error_partials", "dm_finish_iteration", "dm_set_graph", "dm_autotune",
            "dm_get_plan", "dm_batch_create", "dm_batch_iterate", "dm_batch_set_graph", "dm_batch_free",
-           "dm_batch_last_error", "dm_dft2", "dm_fp32_peak", "dm_set_psi_precision", "dm_get_psi_precision", "dm_net_create", "dm_net_param_count", "dm_net_get_params",
+           "dm_batch_last_error", "dm_dft2", "dm_fp32_peak", "dm_set_psi_precision", "dm_get_psi_precision", "dm_set_fourier_form", "dm_get_fourier_form", "dm_net_create", "dm_net_param_count", "dm_net_get_params",
            "dm_net_set_params", "dm_net_forward", "dm_net_gradients", "dm_net_train_step", "dm_net_set_loss",
            "dm_net_free"]
 
@@ -118,6 +119,8 @@ def load(path: str = LIB_PATH):
         "dm_set_graph": (ctypes.c_int, [vp, i32]),
         "dm_autotune": (ctypes.c_int, [vp, i32, dp]),
         "dm_get_plan": (ctypes.c_int, [vp, P(i64)]),
+        "dm_set_fourier_form": (ctypes.c_int, [vp, i32]),
+        "dm_get_fourier_form": (ctypes.c_int, [vp, P(i32)]),
         "dm_batch_create": (ctypes.c_int, [P(vp), P(vp), i32]),
         "dm_batch_iterate": (ctypes.c_int, [vp, i32]),
         "dm_batch_set_graph": (ctypes.c_int, [vp, i32]),
@@ -613,6 +616,18 @@ def dm_get_psi_precision(ctx: Context):
     at = ctypes.c_int64()
     _check(load().dm_get_psi_precision(ctx.handle, ctypes.byref(prec), ctypes.byref(at)), ctx)
     return prec.value, at.value
+
+
+def dm_set_fourier_form(ctx: Context, form: int):
+    """Run the Fourier step in DM_FOURIER_STRIP or DM_FOURIER_SPLIT form (see dm.h)."""
+    return _check(load().dm_set_fourier_form(ctx.handle, int(form)), ctx)
+
+
+def dm_get_fourier_form(ctx: Context) -> int:
+    """The form the next Fourier step runs (DM_FOURIER_STRIP or DM_FOURIER_SPLIT)."""
+    form = ctypes.c_int32()
+    _check(load().dm_get_fourier_form(ctx.handle, ctypes.byref(form)), ctx)
+    return form.value
 
 
 def dm_fp32_peak() -> float:

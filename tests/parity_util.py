@@ -34,7 +34,7 @@ def case(n, modes, grid, step, obj, seed, jitter=1, probe="hg", fwhm=None, photo
 
 
 def run_gpu(s, p0, o0, psi0, n_iter=1, beta=0.8, delta_rel=1e-6, n_inner=1, probe_update_start=0,
-            scratch_bytes=0, use_torch_allocator=None, order="gauss-seidel"):
+            scratch_bytes=0, use_torch_allocator=None, order="gauss-seidel", form=None):
     from paper_1808_10375_gb300 import dm
     h, w = s.obj_shape
     params = dm.dm_params_default(n=s.n, modes=s.modes, views=s.views, obj_h=h, obj_w=w, beta=beta,
@@ -44,6 +44,9 @@ def run_gpu(s, p0, o0, psi0, n_iter=1, beta=0.8, delta_rel=1e-6, n_inner=1, prob
     ctx = dm.dm_init(params, s.pos, s.intensities, p0, o0, use_torch_allocator=use_torch_allocator)
     if psi0 is not None:
         dm.dm_set_exit_waves(ctx, psi0)
+    if form is not None:
+        dm.dm_set_fourier_form(ctx, form)
+        assert dm.dm_get_fourier_form(ctx) == form
     dm.dm_iterate(ctx, n_iter)
     out = dict(psi=dm.dm_get_exit_waves(ctx), probe=dm.dm_get_probe(ctx), obj=dm.dm_get_object(ctx),
                metrics=[dm.dm_get_error(ctx, i) for i in range(n_iter)])
