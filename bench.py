@@ -528,9 +528,12 @@ def run_batch16(args, rank, local):
 def run_dft256(args, rank, local):
     """The batched 256 x 256 2-D DFT (dm_dft2) on the exit waves of the first
     1,000 views of the 8-mode workload (8,000 frames), in the FP32 register-FFT
-    form and the split-BF16 tensor-core form: frames per second, the tensor
-    form's tensor-core FLOP/s against the measured bf16 peak, and each form's
-    relative L2 error against numpy's FP64 FFT on a sample of the frames."""
+    form and the two split-BF16 tensor-core forms (radix-16 stages on mma.sync;
+    dense row GEMMs on tcgen05 with tensor-memory accumulators): frames per
+    second, the tensor forms' tensor-core FLOP/s against the measured bf16
+    peak, and each form's relative L2 error against numpy's FP64 FFT on a
+    sample of the frames.  The line's value and roofline are the tcgen05
+    form's."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -555,7 +558,8 @@ def run_dft256(args, rank, local):
     sample = torch.arange(0, nf, max(1, nf // 48))[:48]
     ref = np.fft.fft2(frames[sample].cpu().numpy().astype(np.complex128))
     res = {}
-    for prec, name in ((dm.DM_DFT_FP32, "fp32_fft"), (dm.DM_DFT_BF16X3, "bf16x3_tensor")):
+    for prec, name in ((dm.DM_DFT_FP32, "fp32_fft"), (dm.DM_DFT_BF16X3, "bf16x3_tensor"),
+                       (dm.DM_DFT_BF16X3_TC05, "bf16x3_tcgen05")):
         for _ in range(args.warmup):
             dm.dm_dft2(frames, work=work, out=out, precision=prec)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -567,20 +571,27 @@ def run_dft256(args, rank, local):
         e1.record()
         torch.cuda.synchronize()
         sec = e0.elapsed_time(e1) / 1e3 / args.steps
+        if prec == dm.DM_DFT_BF16X3_TC05:
+            dm.dm_dft2_check()   # no bounded wait gave up
         got = out[sample].cpu().numpy().astype(np.complex128)
         err = float(np.linalg.norm((got - ref).ravel()) / np.linalg.norm(ref.ravel()))
         res[name] = {"frames_per_s": nf / sec, "ms_per_batch": 1e3 * sec, "rel_l2_vs_fp64": err,
                      "hbm_gbs": nf * s.n * s.n * 32 / sec / 1e9}
-    # tensor-core work of the split form: 4 radix-16 stages, each 12
-    # m16n8k16 products per 8 lines of 16 points
-    flops = nf * s.n * s.n * 4 * (12 * 2 * 16 * 8 * 16) / (8 * 16)
-    tc = res["bf16x3_tensor"]
+    # tensor-core work: the mma.sync form takes 4 radix-16 stages, each 12
+    # m16n8k16 products per 8 lines of 16 points; the tcgen05 form 2 passes of
+    # 256 rows, each 3 products of (1 x 512) by (512 x 512) real matrices
+    flops_mma = nf * s.n * s.n * 4 * (12 * 2 * 16 * 8 * 16) / (8 * 16)
+    flops_tc05 = nf * 2 * s.n * 3 * 2 * (2 * s.n) * (2 * s.n)
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             bf16_peak = float(json.load(f)["bf16_tflops"])
     except Exception:
         bf16_peak = 1900.0
-    tflops = flops / (tc["ms_per_batch"] / 1e3) / 1e12
+    for name, fl in (("bf16x3_tensor", flops_mma), ("bf16x3_tcgen05", flops_tc05)):
+        res[name]["tensor_tflops"] = fl / (res[name]["ms_per_batch"] / 1e3) / 1e12
+        res[name]["tensor_frac_of_measured_bf16"] = res[name]["tensor_tflops"] / bf16_peak
+    tc = res["bf16x3_tcgen05"]
+    tflops = tc["tensor_tflops"]
     if rank == 0:
         print(json.dumps({
             "metric": "frames/s, batched 256x256 2-D DFT", "value": tc["frames_per_s"], "unit": "frames/s",
@@ -590,7 +601,9 @@ def run_dft256(args, rank, local):
                        "error_sample_frames": int(sample.numel())},
             "forms": res,
             "roofline": {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
-                         "frac": tflops / bf16_peak, "kernel": "k_dft256_rows_tc (mma.sync m16n8k16 bf16)"},
+                         "frac": tflops / bf16_peak, "peak_kind": "measured bf16 (MEASURED_PEAKS.json, burst)",
+                         "flops_per_batch": flops_tc05,
+                         "kernel": "k_dft256_rows_tc05 (tcgen05.mma kind::f16, bf16 hi/lo, TMEM accumulators)"},
         }), flush=True)
 
 

@@ -417,9 +417,16 @@ int dm_finish_iteration(dm_ctx* ctx, const double* sums);
  * precision DM_DFT_FP32: the FP32 register radix-16 FFT of the Fourier step.
  * precision DM_DFT_BF16X3: each 16-point stage on the tensor cores as complex
  *   GEMMs with split BF16 operands (a = hi + lo, three products hi*hi +
- *   hi*lo + lo*hi per real GEMM) and FP32 accumulation; the twiddles between
- *   stages in FP32.  Its error is bounded as stated in the tests (relative L2
- *   against an FP64 DFT).
+ *   hi*lo + lo*hi per real GEMM) and FP32 accumulation (mma.sync); the
+ *   twiddles between stages in FP32.
+ * precision DM_DFT_BF16X3_TC05: each 256-point row transform as one dense
+ *   complex GEMM (the row's 512 floats times the real-ified 512 x 512 DFT
+ *   matrix) on the 5th-generation tensor cores (tcgen05.mma with its
+ *   accumulators in tensor memory, the matrix streamed by TMA), with the same
+ *   split BF16 operands and FP32 accumulation.  Each of its CTAs holds 512
+ *   tensor-memory columns, so it runs one CTA per SM.
+ * The two tensor-core forms' errors are bounded as stated in the tests
+ * (relative L2 against an FP64 DFT).
  * in, work, out: device pointers on the current device, [frames][N][N]
  * complex (float pairs); work is caller-owned scratch of the same size and
  * must alias neither in nor out; out may equal in.  Work is enqueued on
@@ -428,8 +435,15 @@ int dm_finish_iteration(dm_ctx* ctx, const double* sums);
  * capture.  Errors: DM_EINVAL, DM_ECUDA (message in dm_last_error(NULL)). */
 #define DM_DFT_FP32 0
 #define DM_DFT_BF16X3 1
+#define DM_DFT_BF16X3_TC05 2
 int dm_dft2(const float* in, float* work, float* out, int32_t n, int32_t frames, int32_t inverse,
             int32_t precision, void* stream);
+
+/* Waits for the current device to finish its work, then reports whether a
+ * bounded wait inside a DM_DFT_BF16X3_TC05 transform gave up (1 s; its
+ * result is then not valid) since the last check: DM_ETIMEOUT, else DM_OK,
+ * and clears the record.  DM_ECUDA on a CUDA error. */
+int dm_dft2_check(void);
 
 /* Learned warm start: a small convolutional encoder-decoder mapping one
  * recorded diffraction amplitude (128 x 128, float) to the object amplitude

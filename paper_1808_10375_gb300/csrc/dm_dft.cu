@@ -355,7 +355,7 @@ extern "C" int dm_dft2(const float* in, float* work, float* out, int32_t n, int3
     return DM_EINVAL;
   }
   if (!in || !work || !out) { set_global_error("dm_dft2: a pointer is NULL"); return DM_EINVAL; }
-  if (precision != DM_DFT_FP32 && precision != DM_DFT_BF16X3) {
+  if (precision != DM_DFT_FP32 && precision != DM_DFT_BF16X3 && precision != DM_DFT_BF16X3_TC05) {
     set_global_error("dm_dft2: unknown precision");
     return DM_EINVAL;
   }
@@ -363,21 +363,43 @@ extern "C" int dm_dft2(const float* in, float* work, float* out, int32_t n, int3
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   static std::mutex mu;
-  static bool ready[256] = {};
-  if (e == cudaSuccess && dev >= 0 && dev < 256) {
+  static bool ready[64] = {}, ready_tc[64] = {};
+  if (e == cudaSuccess && (dev < 0 || dev >= 64)) e = cudaErrorInvalidDevice;
+  if (e == cudaSuccess) {
     std::lock_guard<std::mutex> lock(mu);
     if (!ready[dev]) {
       e = prepare_dft256(static_cast<cudaStream_t>(stream));
       if (e == cudaSuccess) ready[dev] = true;
     }
+    if (e == cudaSuccess && precision == DM_DFT_BF16X3_TC05 && !ready_tc[dev]) {
+      e = prepare_dft256_tc05(static_cast<cudaStream_t>(stream));
+      if (e == cudaSuccess) ready_tc[dev] = true;
+    }
   }
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && precision == DM_DFT_BF16X3_TC05)
+    e = launch_dft256_tc05(reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(work),
+                           reinterpret_cast<float2*>(out), frames, inverse != 0, static_cast<cudaStream_t>(stream));
+  else if (e == cudaSuccess)
     e = launch_dft256(reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(work),
                       reinterpret_cast<float2*>(out), frames, inverse != 0, precision,
                       static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) {
     set_global_error(cudaGetErrorString(e));
     return DM_ECUDA;
+  }
+  return DM_OK;
+}
+
+extern "C" int dm_dft2_check(void) {
+  int timed_out = 0;
+  const cudaError_t e = dmk::dft256_tc05_status(&timed_out);
+  if (e != cudaSuccess) {
+    dmk::set_global_error(cudaGetErrorString(e));
+    return DM_ECUDA;
+  }
+  if (timed_out) {
+    dmk::set_global_error("dm_dft2: a bounded wait of the tcgen05 form gave up");
+    return DM_ETIMEOUT;
   }
   return DM_OK;
 }

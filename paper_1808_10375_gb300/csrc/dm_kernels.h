@@ -237,6 +237,13 @@ cudaError_t launch_wait_selftest(const int* flag, int* status, int* ok, cudaStre
 cudaError_t prepare_dft256(cudaStream_t s);
 cudaError_t launch_dft256(const float2* in, float2* work, float2* out, int frames, bool inverse, int precision,
                           cudaStream_t s);
+// The tcgen05 form (dm_dft_tc.cu): its table, TMA view and shared-memory
+// limit once per device, the two passes, and the status word of its bounded
+// waits (synchronises the device, then reads and clears it).
+cudaError_t prepare_dft256_tc05(cudaStream_t s);
+cudaError_t launch_dft256_tc05(const float2* in, float2* work, float2* out, int frames, bool inverse,
+                               cudaStream_t s);
+cudaError_t dft256_tc05_status(int* timed_out);
 
 // Message returned by dm_last_error(NULL) (calls made without a context).
 void set_global_error(const char* msg);

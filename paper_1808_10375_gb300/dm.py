@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libptycho_dm.so")
 DM_OK, DM_EINVAL, DM_ENOMEM, DM_ECUDA, DM_ENONFINITE, DM_ETIMEOUT = 0, -1, -2, -3, -4, -5
 DM_HOST, DM_DEVICE = 0, 1
 DM_STEP_FOURIER, DM_STEP_OBJECT, DM_STEP_PROBE = 0, 1, 2
-DM_DFT_FP32, DM_DFT_BF16X3 = 0, 1
+DM_DFT_FP32, DM_DFT_BF16X3, DM_DFT_BF16X3_TC05 = 0, 1, 2
 DM_ORDER_GAUSS_SEIDEL, DM_ORDER_JACOBI = 0, 1
 DM_PSI_FP32, DM_PSI_FP16 = 0, 1
 DM_FOURIER_STRIP, DM_FOURIER_SPLIT = 0, 1
@@ -64,7 +64,7 @@ EXPORTS = ["dm_params_default", "dm_init", "dm_iterate", "dm_run_step", "dm_get_
            "dm_object_partials", "dm_object_apply", "dm_probe_partials", "dm_probe_apply",
            "dm_fourier_error_partials", "dm_finish_iteration", "dm_set_graph", "dm_autotune",
            "dm_get_plan", "dm_batch_create", "dm_batch_iterate", "dm_batch_set_graph", "dm_batch_free",
-           "dm_batch_last_error", "dm_dft2", "dm_fp32_peak", "dm_set_psi_precision", "dm_get_psi_precision", "dm_set_fourier_form", "dm_get_fourier_form", "dm_net_create", "dm_net_param_count", "dm_net_get_params",
+           "dm_batch_last_error", "dm_dft2", "dm_dft2_check", "dm_fp32_peak", "dm_set_psi_precision", "dm_get_psi_precision", "dm_set_fourier_form", "dm_get_fourier_form", "dm_net_create", "dm_net_param_count", "dm_net_get_params",
            "dm_net_set_params", "dm_net_forward", "dm_net_gradients", "dm_net_train_step", "dm_net_set_loss",
            "dm_net_free"]
 
@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH):
         "dm_batch_free": (None, [vp]),
         "dm_batch_last_error": (ctypes.c_char_p, [vp]),
         "dm_dft2": (ctypes.c_int, [vp, vp, vp, i32, i32, i32, i32, vp]),
+        "dm_dft2_check": (ctypes.c_int, []),
         "dm_net_create": (ctypes.c_int, [P(vp), i32, ctypes.c_uint64]),
         "dm_net_param_count": (i64, [vp]),
         "dm_net_get_params": (ctypes.c_int, [vp, f32p]),
@@ -348,6 +349,14 @@ def dm_dft2(x, work=None, out=None, inverse=False, precision=DM_DFT_FP32, stream
     if rc != DM_OK:
         raise DMError(rc, (load().dm_last_error(None) or b"").decode())
     return out
+
+
+def dm_dft2_check():
+    """Synchronise the device and raise DMError(DM_ETIMEOUT) if a bounded wait
+    of the tcgen05 DFT form gave up since the last check (see dm.h)."""
+    rc = load().dm_dft2_check()
+    if rc != DM_OK:
+        raise DMError(rc, (load().dm_last_error(None) or b"").decode())
 
 
 class Net:
