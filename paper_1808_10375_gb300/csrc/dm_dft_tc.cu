@@ -16,8 +16,8 @@
 // between stages, and the tensor cores have the arithmetic to spare.
 //
 // Data movement: the B planes (hi and lo, both directions) are a device
-// table streamed by TMA in the 128-byte-swizzled K-major layout, 64 K values
-// per pipeline stage; four producer warps (one thread per row) load the
+// table streamed by TMA in the 64-byte-swizzled K-major layout, 32 K values
+// per pipeline stage in a ring of four; four producer warps (one thread per row) load the
 // rows' FP32 values, split them and write A in the same layout; one thread
 // issues the MMAs and the TMA loads; the producer warps then read the
 // accumulators back (tcgen05.ld, lane = row) and store them transposed, one
@@ -41,14 +41,17 @@ constexpr int kTN = 256;                  // transform length
 constexpr int kTK = 2 * kTN;              // real K (= real N) of the GEMM
 constexpr int kTM = 128;                  // rows per CTA (MMA M)
 constexpr int kTNh = 256;                 // MMA N (half of the output columns)
-constexpr int kStageK = 64;               // real K per pipeline stage (one 128-byte swizzle row)
-constexpr int kStages = kTK / kStageK;    // 8 stages per N half
-constexpr int kRing = 2;                  // stage buffers
-constexpr int kABytes = kTM * kStageK * 2;     // 16 KB: one A plane of a stage
-constexpr int kBBytes = kTNh * kStageK * 2;    // 32 KB: one B plane of a stage
+constexpr int kStageK = 32;               // real K per pipeline stage (one 64-byte swizzle row)
+constexpr int kStages = kTK / kStageK;    // 16 stages per N half
+constexpr int kRing = 4;                  // stage buffers
+constexpr int kRowB = kStageK * 2;        // bytes of one operand row in a stage (the swizzle span)
+constexpr int kAtomB = 8 * kRowB;         // bytes of one 8-row swizzle atom (the MMA's stride offset)
+constexpr int kABytes = kTM * kStageK * 2;     // 8 KB: one A plane of a stage
+constexpr int kBBytes = kTNh * kStageK * 2;    // 16 KB: one B plane of a stage
 constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;   // A hi, A lo, B hi, B lo
-constexpr int kProducers = 128;           // producer / epilogue threads (warps 0-3)
-constexpr int kTcThreads = kProducers + 32;   // + the MMA warp
+constexpr int kProducers = 128;           // producer threads (warps 0-3)
+constexpr int kEpilogue = 128;            // epilogue threads (warps 5-8)
+constexpr int kTcThreads = kProducers + 32 + kEpilogue;   // + the MMA warp (warp 4)
 constexpr size_t kTcSmem = 1024 + (size_t)kRing * kStageBytes;
 
 // B planes: [direction][hi, lo][n][k] as BF16, n the real output index and
@@ -145,27 +148,33 @@ __device__ __forceinline__ void split8(const float4& u, const float4& w, uint4& 
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// One pass: the 256-point DFT of the 128 rows r0.. of frame f, stored
-// transposed (out[f][q][r]).  Block: warps 0-3 produce A and read the
-// accumulators back (thread = row), warp 4 allocates tensor memory and its
-// lane 0 issues the B loads and the MMAs.
+// One pass: the 256-point DFT of every 128-row tile (rows r0.. of frame f),
+// stored transposed (out[f][q][r]).  Persistent: CTA c takes tiles c, c +
+// grid, ...  Warps 0-3 produce A; warp 4 allocates tensor memory and its
+// lane 0 issues the B loads and the MMAs; warps 5-8 read the accumulators
+// back (warp w reads tensor-memory lanes 32 (w % 4) .., thread = row) and
+// store them.  Each N half has its own 256 accumulator columns with a full
+// and an empty barrier, so one half is drained while the MMAs of the other
+// half (or of the next tile) run.
 template <bool INV>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_dft256_rows_tc05(const __grid_constant__ CUtensorMap tmB, const float2* __restrict__ in,
-                       float2* __restrict__ out) {
+                       float2* __restrict__ out, int ntiles) {
   extern __shared__ unsigned char tc_raw[];
-  // 1024-byte aligned stages: the 128-byte swizzle repeats every 1024 bytes
+  // 1024-byte aligned stages (the 64-byte swizzle repeats every 512 bytes)
   unsigned char* base = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
-  __shared__ __align__(8) uint64_t full[kRing], empty[kRing], done;
+  __shared__ __align__(8) uint64_t full[kRing], empty[kRing], accf[2], acce[2];
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int f = blockIdx.x >> 1, r0 = (blockIdx.x & 1) * kTM;
   if (tid == kProducers) {
     for (int b = 0; b < kRing; ++b) {
       mbar_init(&full[b], kProducers + 1);   // the producers and the B loads' expect_tx
       mbar_init(&empty[b], 1);               // the MMA thread's commit
     }
-    mbar_init(&done, 1);
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(&accf[h], 1);                // the MMA thread's commit: half h complete
+      mbar_init(&acce[h], kEpilogue);        // the epilogue threads: half h drained
+    }
     fence_mbar_init();
   }
   if (warp == 4) tmem_alloc(&s_tmem, 2 * kTNh);
@@ -174,97 +183,120 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   constexpr uint32_t idesc = dmtc::idesc_f16(dmtc::kFmtF32, dmtc::kFmtBF16, dmtc::kFmtBF16, kTM, kTNh);
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nst = my_tiles * 2 * kStages;   // pipeline stages of this CTA
 
   if (warp < 4) {
     // ---- producers: the A planes of every stage ----
-    // Chunk task i (of 1024 per stage: 128 rows x 8 chunks of 8 K values) is
-    // row i / 8, chunk i % 8; thread t takes tasks t + 128 it, so 8
-    // consecutive threads read one row's 256 contiguous bytes (coalesced) and
-    // write its 8 chunks (the swizzle spreads them over all banks).  The next
+    // Chunk task i (of 512 per stage: 128 rows x 4 chunks of 8 K values) is
+    // row i / 4, chunk i % 4; thread t takes tasks t + 128 it, so 4
+    // consecutive threads read one row's 128 contiguous bytes (coalesced) and
+    // write its 4 chunks (the swizzle spreads them over the banks).  The next
     // stage's values are loaded while the current ones are converted.
-    const float4* rows = reinterpret_cast<const float4*>(in + ((size_t)f * kTN + r0) * kTN);
-    float4 buf[2][2 * 8];
-    auto load = [&](int g, float4 (&d)[2 * 8]) {
-      const int s = g % kStages;
+    constexpr int kCh = kStageK / 8;   // chunks per row and stage
+    constexpr int kIt = kTM * kCh / kProducers;
+    float4 buf[2][2 * kIt];
+    auto load = [&](int g, float4 (&d)[2 * kIt]) {
+      const int tile = blockIdx.x + (g / (2 * kStages)) * gridDim.x, s = g % kStages;
+      const float4* rows = reinterpret_cast<const float4*>(in + (size_t)tile * kTM * kTN);
 #pragma unroll
-      for (int it = 0; it < 8; ++it) {
-        const int id = it * kProducers + tid, row = id >> 3, j = id & 7;
+      for (int it = 0; it < kIt; ++it) {
+        const int id = it * kProducers + tid, row = id / kCh, j = id % kCh;
         const float4* p = rows + (size_t)row * (kTN / 2) + s * (kStageK / 4) + 2 * j;
         d[2 * it] = __ldg(p);
         d[2 * it + 1] = __ldg(p + 1);
       }
     };
-    auto store = [&](int g, const float4 (&d)[2 * 8]) {
+    auto store = [&](int g, const float4 (&d)[2 * kIt]) {
       const int b = g % kRing;
       if (g >= kRing) tc_wait(&empty[b], ((g / kRing) - 1) & 1);   // the MMAs of stage g - kRing are done
       unsigned char* ah = base + (size_t)b * kStageBytes;
 #pragma unroll
-      for (int it = 0; it < 8; ++it) {
-        const int id = it * kProducers + tid, row = id >> 3, j = id & 7;
+      for (int it = 0; it < kIt; ++it) {
+        const int id = it * kProducers + tid, row = id / kCh, j = id % kCh;
         uint4 hi, lo;
         split8(d[2 * it], d[2 * it + 1], hi, lo);
-        const int off = row * 128 + ((j ^ (row & 7)) << 4);   // 128-byte swizzle
+        // 64-byte swizzle: 16-byte chunk ^ bits 7-8 of the row's offset
+        const int off = row * kRowB + ((j ^ ((row >> 1) & 3)) << 4);
         *reinterpret_cast<uint4*>(ah + off) = hi;
         *reinterpret_cast<uint4*>(ah + kABytes + off) = lo;
       }
       fence_proxy_async_smem();   // visible to the tensor cores (async proxy)
       mbar_arrive(&full[b]);
     };
-    load(0, buf[0]);
-#pragma unroll
-    for (int g = 0; g < 2 * kStages; ++g) {
-      if (g + 1 < 2 * kStages) load(g + 1, buf[(g + 1) & 1]);
-      store(g, buf[g & 1]);
+    if (nst > 0) load(0, buf[0]);
+    for (int g = 0; g < nst; g += 2) {   // two stages per trip: the buffers' roles stay compile-time
+      if (g + 1 < nst) load(g + 1, buf[1]);
+      store(g, buf[0]);
+      if (g + 1 < nst) {
+        if (g + 2 < nst) load(g + 2, buf[0]);
+        store(g + 1, buf[1]);
+      }
     }
-    const int r = tid;   // the epilogue: thread = row (tensor-memory lane)
+  } else if (warp == 4) {
+    if (lane == 0) {
+      // ---- B loads and MMAs (one thread) ----
+      const uint64_t pol = l2_policy_evict_last();
+      const int plane = INV ? 2 : 0;
+      auto load_b = [&](int g) {
+        const int b = g % kRing, s = g % kStages, h = (g / kStages) & 1;
+        unsigned char* bh = base + (size_t)b * kStageBytes + 2 * kABytes;
+        mbar_arrive_expect_tx(&full[b], 2 * kBBytes);
+        tma_load_3d_hint(bh, &tmB, s * kStageK, h * kTNh, plane, &full[b], pol);
+        tma_load_3d_hint(bh + kBBytes, &tmB, s * kStageK, h * kTNh, plane + 1, &full[b], pol);
+      };
+      if (nst > 0) load_b(0);
+      for (int g = 0; g < nst; ++g) {
+        const int b = g % kRing, s = g % kStages, h = (g / kStages) & 1, i = g / (2 * kStages);
+        if (g + 1 < nst) {
+          // the next stage's buffer held stage g + 1 - kRing: its MMAs must be done
+          if (g + 1 >= kRing) tc_wait(&empty[(g + 1) % kRing], (((g + 1) / kRing) - 1) & 1);
+          load_b(g + 1);
+        }
+        if (s == 0 && i > 0) {   // half h of the previous tile has been drained
+          tc_wait(&acce[h], (i - 1) & 1);
+          tc_fence_after();
+        }
+        tc_wait(&full[b], (g / kRing) & 1);
+        tc_fence_after();
+        const uint32_t sa = smem_u32(base + (size_t)b * kStageBytes);
+        const uint32_t d = tmem + (uint32_t)(h * kTNh);
+#pragma unroll
+        for (int kk = 0; kk < kStageK / 16; ++kk) {
+          const uint32_t o = 32u * kk;   // 16 BF16 K values further along the swizzle row
+          const uint64_t ahd = dmtc::smem_desc(sa + o, 16, kAtomB, dmtc::kSw64);
+          const uint64_t ald = dmtc::smem_desc(sa + kABytes + o, 16, kAtomB, dmtc::kSw64);
+          const uint64_t bhd = dmtc::smem_desc(sa + 2 * kABytes + o, 16, kAtomB, dmtc::kSw64);
+          const uint64_t bld = dmtc::smem_desc(sa + 2 * kABytes + kBBytes + o, 16, kAtomB, dmtc::kSw64);
+          tc_mma_f16(d, ahd, bhd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+          tc_mma_f16(d, ahd, bld, idesc, 1u);
+          tc_mma_f16(d, ald, bhd, idesc, 1u);
+        }
+        tc_commit(&empty[b]);
+        if (s == kStages - 1) tc_commit(&accf[h]);   // half h of this tile is complete
+      }
+    }
+  } else {
     // ---- epilogue: accumulators back, stored transposed ----
-    tc_wait(&done, 0);
-    tc_fence_after();
-    float2* dst = out + (size_t)f * kTN * kTN + r0 + r;
-    for (int cc = 0; cc < kTK / 32; ++cc) {
-      float v[32];
-      tmem_ld32(dmtc::tmem_addr(tmem, 32 * warp, 32 * cc), v);
+    const int q4 = warp & 3, r = 32 * q4 + lane;   // tensor-memory lane = row of the tile
+    for (int i = 0; i < my_tiles; ++i) {
+      const int tile = blockIdx.x + i * gridDim.x;
+      const int f = tile >> 1, r0 = (tile & 1) * kTM;
+      float2* dst = out + (size_t)f * kTN * kTN + r0 + r;
+      for (int h = 0; h < 2; ++h) {
+        tc_wait(&accf[h], i & 1);
+        tc_fence_after();
+        for (int cc = 0; cc < kTNh / 32; ++cc) {
+          float v[32];
+          tmem_ld32(dmtc::tmem_addr(tmem, 32 * q4, h * kTNh + 32 * cc), v);
+          const int q0 = (h * kTNh + 32 * cc) / 2;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) __stcs(dst + (size_t)(16 * cc + i) * kTN, make_float2(v[2 * i], v[2 * i + 1]));
-    }
-    tc_fence_before();
-  } else if (lane == 0) {
-    // ---- B loads and MMAs (one thread) ----
-    const uint64_t pol = l2_policy_evict_last();
-    const int plane = INV ? 2 : 0;
-    auto load_b = [&](int g) {
-      const int b = g % kRing, s = g % kStages, h = g / kStages;
-      unsigned char* bh = base + (size_t)b * kStageBytes + 2 * kABytes;
-      mbar_arrive_expect_tx(&full[b], 2 * kBBytes);
-      tma_load_3d_hint(bh, &tmB, s * kStageK, h * kTNh, plane, &full[b], pol);
-      tma_load_3d_hint(bh + kBBytes, &tmB, s * kStageK, h * kTNh, plane + 1, &full[b], pol);
-    };
-    load_b(0);
-    for (int g = 0; g < 2 * kStages; ++g) {
-      const int b = g % kRing, s = g % kStages, h = g / kStages;
-      if (g + 1 < 2 * kStages) {
-        // the next stage's buffer held stage g + 1 - kRing: its MMAs must be done
-        if (g + 1 >= kRing) tc_wait(&empty[(g + 1) % kRing], (((g + 1) / kRing) - 1) & 1);
-        load_b(g + 1);
+          for (int e = 0; e < 16; ++e) __stcs(dst + (size_t)(q0 + e) * kTN, make_float2(v[2 * e], v[2 * e + 1]));
+        }
+        tc_fence_before();
+        mbar_arrive(&acce[h]);
       }
-      tc_wait(&full[b], (g / kRing) & 1);
-      tc_fence_after();
-      const uint32_t sa = smem_u32(base + (size_t)b * kStageBytes);
-      const uint32_t d = tmem + (uint32_t)(h * kTNh);
-#pragma unroll
-      for (int kk = 0; kk < kStageK / 16; ++kk) {
-        const uint32_t o = 32u * kk;   // 16 BF16 K values further along the swizzle row
-        const uint64_t ahd = dmtc::smem_desc(sa + o, 16, 1024, dmtc::kSw128);
-        const uint64_t ald = dmtc::smem_desc(sa + kABytes + o, 16, 1024, dmtc::kSw128);
-        const uint64_t bhd = dmtc::smem_desc(sa + 2 * kABytes + o, 16, 1024, dmtc::kSw128);
-        const uint64_t bld = dmtc::smem_desc(sa + 2 * kABytes + kBBytes + o, 16, 1024, dmtc::kSw128);
-        tc_mma_f16(d, ahd, bhd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-        tc_mma_f16(d, ahd, bld, idesc, 1u);
-        tc_mma_f16(d, ald, bhd, idesc, 1u);
-      }
-      tc_commit(&empty[b]);
     }
-    tc_commit(&done);
   }
   __syncthreads();
   if (warp == 4) {
@@ -304,7 +336,7 @@ cudaError_t prepare_dft256_tc05(cudaStream_t s) {
   const cuuint32_t box[3] = {(cuuint32_t)kStageK, (cuuint32_t)kTNh, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = encode(&g_tc_map[dev], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, table, dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -315,11 +347,15 @@ cudaError_t launch_dft256_tc05(const float2* in, float2* work, float2* out, int 
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const CUtensorMap& m = g_tc_map[dev];
+  int sms = 0;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int ntiles = 2 * frames;                    // 128-row tiles per pass
+  const int grid = ntiles < sms ? ntiles : sms;     // persistent, one CTA per SM
   for (int pass = 0; pass < 2; ++pass) {
     const float2* a = pass == 0 ? in : work;
     float2* b = pass == 0 ? work : out;
-    if (inverse) k_dft256_rows_tc05<true><<<2 * frames, kTcThreads, kTcSmem, s>>>(m, a, b);
-    else k_dft256_rows_tc05<false><<<2 * frames, kTcThreads, kTcSmem, s>>>(m, a, b);
+    if (inverse) k_dft256_rows_tc05<true><<<grid, kTcThreads, kTcSmem, s>>>(m, a, b, ntiles);
+    else k_dft256_rows_tc05<false><<<grid, kTcThreads, kTcSmem, s>>>(m, a, b, ntiles);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
