@@ -275,6 +275,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_commit(&empty[b]);
         if (s == kStages - 1) tc_commit(&accf[h]);   // half h of this tile is complete
       }
+      // every MMA has completed before the tensor memory is freed (already so
+      // unless a bounded wait above gave up)
+      if (nst > 0) tc_wait(&empty[(nst - 1) % kRing], ((nst - 1) / kRing) & 1);
     }
   } else {
     // ---- epilogue: accumulators back, stored transposed ----

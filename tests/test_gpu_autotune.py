@@ -36,3 +36,27 @@ def test_autotune_keeps_state_and_parity():
              metrics=[dm.dm_get_error(ctx, 0)])
     dm.dm_free(ctx)
     compare(g, run_oracle(s, p0, o0, psi0))
+
+
+def test_autotune_chooses_between_the_fourier_forms():
+    # a 256 x 256, 8-mode scan has both forms: the autotuner times both and
+    # keeps one; whichever it keeps, state is unchanged and parity holds
+    from paper_1808_10375_gb300 import dm
+    s, p0, o0, psi0 = case(256, 8, (3, 3), 18, (320, 330), 62)
+    h, w = s.obj_shape
+    params = dm.dm_params_default(n=s.n, modes=s.modes, views=s.views, obj_h=h, obj_w=w)
+    ctx = dm.dm_init(params, s.pos, s.intensities, p0, o0)
+    dm.dm_set_exit_waves(ctx, psi0)
+    best = dm.dm_autotune(ctx, sample_views=s.views)
+    form = dm.dm_get_fourier_form(ctx)
+    plan = dm.dm_get_plan(ctx)
+    print("form", form, "plan", plan, f"best {best:.3f} ms")
+    assert best > 0 and form in (dm.DM_FOURIER_STRIP, dm.DM_FOURIER_SPLIT)
+    if form == dm.DM_FOURIER_SPLIT:
+        assert plan["strips_per_column_task"] == 0 and plan["strip_buffers"] == 3
+    assert np.array_equal(dm.dm_get_exit_waves(ctx), psi0)
+    dm.dm_iterate(ctx, 1)
+    g = dict(psi=dm.dm_get_exit_waves(ctx), probe=dm.dm_get_probe(ctx), obj=dm.dm_get_object(ctx),
+             metrics=[dm.dm_get_error(ctx, 0)])
+    dm.dm_free(ctx)
+    compare(g, run_oracle(s, p0, o0, psi0))
