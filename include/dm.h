@@ -260,12 +260,13 @@ const char* dm_kernel_name(int32_t kernel);
 int dm_set_graph(dm_ctx* ctx, int32_t enable);
 
 /* Choose the Fourier-step plan by measurement: every distinct combination
- * of scratch-ring size (48, 64, 96, 128 MiB), column-task size (64, 128,
+ * of scratch-ring size (48, 64, 96, 128, 160, 192 MiB), column-task size (64, 128,
  * 256 KiB of scratch) and strip buffers (2, 3) is timed on the first
  * sample_views views of the context (one warm-up and three timed runs of the
  * Fourier kernel each); where the scan has the split form (and the exit-wave
- * change is not tracked), that form is timed too at each ring size, so the
- * choice covers the form as well (dm_get_fourier_form reports it).  The
+ * change is not tracked), that form is timed too at each ring size (48 to
+ * 192 MiB), so the choice covers the form as well (dm_get_fourier_form
+ * reports it).  The
  * fastest is kept for the whole scan.  The exit
  * waves of the sample views are restored afterwards; the object sources are
  * recomputed by the next iteration, so results are unchanged.  Temporary
@@ -292,9 +293,12 @@ int dm_get_plan(const dm_ctx* ctx, int64_t* out);
  * tasks, whose work items are 16 columns x 16 rows x 8 modes; the mode sum
  * of F_c is then a warp-shuffle reduction.  It keeps the intensities in a
  * second layout as well (4 N^2 bytes more per view).  The exit-wave change
- * (dm_set_psi_error) and dm_batch iterations run the strip form.  Contexts
- * start in the strip form; dm_autotune times both where both exist and keeps
- * the faster, and dm_set_fourier_form selects one explicitly
+ * (dm_set_psi_error) and dm_batch iterations run the strip form.  The split
+ * form has a scratch ring of its own size (160 MiB by default: more views per
+ * chunk let its tasks overlap more; dm_params.scratch_bytes, when set, sizes
+ * both).  Contexts that can run the split form start with it; dm_autotune
+ * times both forms where both exist and keeps the faster, and
+ * dm_set_fourier_form selects one explicitly
  * (DM_EINVAL for DM_FOURIER_SPLIT on other shapes); it synchronises and
  * drops captured iteration graphs.  dm_get_fourier_form
  * reports the form the next Fourier step runs. */

@@ -20,6 +20,10 @@
 namespace {
 
 constexpr size_t kScratchBudget = 96ull << 20;   // L2-resident Fourier scratch
+// The split form's default ring: its row and inverse row tasks wait at block
+// barriers, and more views per chunk give the SM other work meanwhile (at
+// 256^2 x 8 modes, 10 views per chunk: 48.7 ms against 53.5 with 6).
+constexpr size_t kSplitScratchBudget = 160ull << 20;
 constexpr size_t kColumnSmemBudget = 100u << 10; // column strips in shared memory
 constexpr size_t kColumnTaskBytes = 128u << 10;  // scratch bytes per column task
 constexpr int kFourierLag = 1;                   // stages between task kinds
@@ -28,9 +32,10 @@ thread_local std::string g_init_error;
 
 // The tunable parts of the Fourier-step plan.
 struct FourierKnobs {
-  size_t budget;      // scratch ring bytes
+  size_t budget;      // scratch ring bytes (strip form)
   size_t task_bytes;  // scratch bytes per column task (sets the strips per task)
   int max_bufs;       // strip buffers of a column task, at most (1 to kMaxStripBufs)
+  size_t split_budget;   // scratch ring bytes of the split form
 };
 
 struct TimedLaunch {
@@ -273,7 +278,7 @@ bool valid_n(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 2
 
 FourierKnobs default_knobs(const dm_ctx* c) {
   return {c->p.scratch_bytes > 0 ? (size_t)c->p.scratch_bytes : kScratchBudget, kColumnTaskBytes,
-          dmk::kMaxStripBufs};
+          dmk::kMaxStripBufs, c->p.scratch_bytes > 0 ? (size_t)c->p.scratch_bytes : kSplitScratchBudget};
 }
 
 // Host part of the plan for the first J views: the pipelined task order
@@ -317,7 +322,7 @@ int fourier_schedule(dm_ctx* c, int J, const FourierKnobs& k, dmk::FourierArgs& 
   a.lag = kFourierLag;
   a.nslot = 2 * a.lag + 2;
   const size_t view_bytes = (size_t)M * N * N * sizeof(float2);
-  size_t B = k.budget / ((size_t)a.nslot * view_bytes);
+  size_t B = (split ? k.split_budget : k.budget) / ((size_t)a.nslot * view_bytes);
   B = std::max<size_t>(1, std::min<size_t>(B, (size_t)J));
   a.B = (int)B;
   a.nchunks = (J + a.B - 1) / a.B;
@@ -430,7 +435,10 @@ int plan_fourier(dm_ctx* c, const FourierKnobs& k) {
   std::vector<int> off;
   int rc;
   if ((rc = fourier_schedule(c, c->J, k, a, off, c->fsmem, c->fgrid))) return rc;
-  if ((rc = alloc_n(c, &c->scratch, scratch_elems(a)))) return rc;
+  // the split form has a ring of its own size (split_budget) in the same buffer
+  std::vector<int> soff;
+  if (c->split_ok && (rc = fourier_schedule(c, c->J, k, c->fs, soff, c->fssmem, c->fsgrid, true))) return rc;
+  if ((rc = alloc_n(c, &c->scratch, std::max(scratch_elems(a), c->split_ok ? scratch_elems(c->fs) : 0)))) return rc;
   if ((rc = alloc_n(c, &c->stage_off, off.size()))) return rc;
   // the single-scan kernels count completed tasks per view, the batched one
   // per chunk (at most one per view)
@@ -442,10 +450,7 @@ int plan_fourier(dm_ctx* c, const FourierKnobs& k) {
   DM_CUDA(c, cudaStreamSynchronize(c->stream));  // `off` is a host temporary
   if ((rc = encode_scratch_map(c, a, c->scratch, c->tmap_s))) return rc;
   if (c->split_ok) {
-    // the split form with the same ring (same views per chunk and slots)
     dmk::FourierArgs& s = c->fs;
-    std::vector<int> soff;
-    if ((rc = fourier_schedule(c, c->J, k, s, soff, c->fssmem, c->fsgrid, true))) return rc;
     if ((rc = alloc_n(c, &c->stage_off_s, soff.size()))) return rc;
     DM_CUDA(c, cudaMemcpyAsync(c->stage_off_s, soff.data(), soff.size() * sizeof(int), cudaMemcpyHostToDevice,
                                c->stream));
@@ -757,7 +762,9 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   DM_TRY(alloc_n(c, &c->cview, (size_t)J * nn));
   DM_TRY(alloc_n(c, &c->istrip, (size_t)J * nn));
   c->split_ok = N == dmk::kSplitN && M == dmk::kSplitModes;
-  c->form = DM_FOURIER_STRIP;   // the faster form on the 10,000-view workload; dm_autotune may pick the other
+  // the split form where it exists (faster on the 10,000-view 8-mode workload
+  // with its own ring size); dm_autotune may pick the other
+  c->form = c->split_ok ? DM_FOURIER_SPLIT : DM_FOURIER_STRIP;
   if (c->split_ok) DM_TRY(alloc_n(c, &c->isplit, (size_t)J * nn));
   DM_TRY(alloc_n(c, &c->probe[0], (size_t)M * nn));
   DM_TRY(alloc_n(c, &c->probe[1], (size_t)M * nn));
@@ -978,11 +985,13 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
   // the split form (where the scan has it, and unless the exit-wave change
   // is tracked) competes with the strip plans; its only knob is the ring
   for (int split = 0; split <= (c->split_ok && !c->psi_err ? 1 : 0); ++split)
-    for (size_t mb : {48, 64, 96, 128})
+    for (size_t mb : {48, 64, 96, 128, 160, 192})
       for (size_t kb : {64, 128, 256})
         for (int b : {2, 3}) {
           Plan pl;
-          pl.k = FourierKnobs{mb << 20, kb << 10, b};
+          // a plan of one form carries the current ring size of the other
+          pl.k = split ? FourierKnobs{c->knobs.budget, c->knobs.task_bytes, c->knobs.max_bufs, mb << 20}
+                       : FourierKnobs{mb << 20, kb << 10, b, c->knobs.split_budget};
           pl.split = split != 0;
           if ((rc = fourier_schedule(c, Js, pl.k, pl.a, pl.off, pl.smem, pl.grid, pl.split))) return rc;
           bool dup = false;
@@ -1070,8 +1079,9 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
 int dm_get_plan(const dm_ctx* c, int64_t* out) {
   if (!c || !out) return DM_EINVAL;
   const bool split = use_split(c);
-  out[0] = (int64_t)scratch_elems(c->fa) * (int64_t)sizeof(float2);
-  out[1] = c->fa.B;
+  const dmk::FourierArgs& a = split ? c->fs : c->fa;
+  out[0] = (int64_t)scratch_elems(a) * (int64_t)sizeof(float2);
+  out[1] = a.B;
   out[2] = split ? 0 : c->fa.SPG;
   out[3] = split ? dmk::kSplitBufs : c->fa.strip_bufs;
   out[4] = split ? c->fsgrid : c->fgrid;

@@ -83,12 +83,14 @@ def test_form_selection_rules():
     with pytest.raises(dm.DMError):
         dm.dm_set_fourier_form(ctx, dm.DM_FOURIER_SPLIT)
     dm.dm_free(ctx)
-    # 256 x 256 with 8 modes starts in the strip form and can switch; tracking
+    # 256 x 256 with 8 modes starts in the split form and can switch; tracking
     # the exit-wave change runs the strip form
     s, p0, o0, psi0 = case(256, 8, (2, 2), 24, (290, 290), 34, probe="hg")
     h, w = s.obj_shape
     params = dm.dm_params_default(n=256, modes=8, views=s.views, obj_h=h, obj_w=w)
     ctx = dm.dm_init(params, s.pos, s.intensities, p0, o0)
+    assert dm.dm_get_fourier_form(ctx) == dm.DM_FOURIER_SPLIT
+    dm.dm_set_fourier_form(ctx, dm.DM_FOURIER_STRIP)
     assert dm.dm_get_fourier_form(ctx) == dm.DM_FOURIER_STRIP
     dm.dm_set_fourier_form(ctx, dm.DM_FOURIER_SPLIT)
     assert dm.dm_get_fourier_form(ctx) == dm.DM_FOURIER_SPLIT
