@@ -294,9 +294,9 @@ int dm_get_plan(const dm_ctx* ctx, int64_t* out);
  * of F_c is then a warp-shuffle reduction.  It keeps the intensities in a
  * second layout as well (4 N^2 bytes more per view).  The exit-wave change
  * (dm_set_psi_error) and dm_batch iterations run the strip form.  The split
- * form has a scratch ring of its own size (160 MiB by default: more views per
- * chunk let its tasks overlap more; dm_params.scratch_bytes, when set, sizes
- * both).  Contexts that can run the split form start with it; dm_autotune
+ * form has a scratch ring of its own (160 MiB of 5 slots by default: more
+ * views in flight let its tasks overlap more; dm_params.scratch_bytes, when
+ * set, sizes both forms' rings).  Contexts that can run the split form start with it; dm_autotune
  * times both forms where both exist and keeps the faster, and
  * dm_set_fourier_form selects one explicitly
  * (DM_EINVAL for DM_FOURIER_SPLIT on other shapes); it synchronises and

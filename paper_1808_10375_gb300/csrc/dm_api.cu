@@ -21,8 +21,8 @@ namespace {
 
 constexpr size_t kScratchBudget = 96ull << 20;   // L2-resident Fourier scratch
 // The split form's default ring: its row and inverse row tasks wait at block
-// barriers, and more views per chunk give the SM other work meanwhile (at
-// 256^2 x 8 modes, 10 views per chunk: 48.7 ms against 53.5 with 6).
+// barriers, and more views in flight give the SM other work meanwhile (at
+// 256^2 x 8 modes: 5 slots of 8 views, 47.5 ms; 4 slots of 6 views, 53.5 ms).
 constexpr size_t kSplitScratchBudget = 160ull << 20;
 constexpr size_t kColumnSmemBudget = 100u << 10; // column strips in shared memory
 constexpr size_t kColumnTaskBytes = 128u << 10;  // scratch bytes per column task
@@ -320,7 +320,12 @@ int fourier_schedule(dm_ctx* c, int J, const FourierKnobs& k, dmk::FourierArgs& 
     a.strip_bufs = 0;
   }
   a.lag = kFourierLag;
-  a.nslot = 2 * a.lag + 2;
+  // Slots: R(s), C(s - lag) and I(s - 2 lag) use 2 lag + 1 of them; each
+  // further slot lets the row tasks run a chunk further ahead of the inverse
+  // row tasks that free their slot.  The split form's row and inverse row
+  // tasks wait at block barriers and gain from that slack (256^2 x 8 modes, 8
+  // views per chunk: 4 slots 50.1 ms, 5 slots 47.5 ms); the strip form does not.
+  a.nslot = 2 * a.lag + (split ? 3 : 2);
   const size_t view_bytes = (size_t)M * N * N * sizeof(float2);
   size_t B = (split ? k.split_budget : k.budget) / ((size_t)a.nslot * view_bytes);
   B = std::max<size_t>(1, std::min<size_t>(B, (size_t)J));
