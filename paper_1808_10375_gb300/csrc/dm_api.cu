@@ -445,8 +445,7 @@ int plan_fourier(dm_ctx* c, const FourierKnobs& k) {
   if (c->split_ok && (rc = fourier_schedule(c, c->J, k, c->fs, soff, c->fssmem, c->fsgrid, true))) return rc;
   if ((rc = alloc_n(c, &c->scratch, std::max(scratch_elems(a), c->split_ok ? scratch_elems(c->fs) : 0)))) return rc;
   if ((rc = alloc_n(c, &c->stage_off, off.size()))) return rc;
-  // the single-scan kernels count completed tasks per view, the batched one
-  // per chunk (at most one per view)
+  // completed tasks are counted per view
   c->counters_bytes = sizeof(int) * (1 + 3 * (size_t)c->J);
   if ((rc = dev_alloc(c, reinterpret_cast<void**>(&c->counters), c->counters_bytes))) return rc;
   if ((rc = alloc_n(c, &c->ef_part, (size_t)c->J * std::max(a.CG, dmk::kSplitN / 16)))) return rc;

@@ -596,9 +596,9 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
     if (sc != scan_prev) { scan_prev = sc; st_prev = 0; }
     const FourierArgs& a = as[sc];
     const int task = gtask - base[sc];
-    int* doneR = a.counters + 1;
-    int* doneC = doneR + a.nchunks;
-    int* doneI = doneC + a.nchunks;
+    int* doneR = a.counters + 1;   // completion counters per view
+    int* doneC = doneR + a.J;
+    int* doneI = doneC + a.J;
     const size_t slot_elems = (size_t)a.B * a.M * N * N;
 
     // Decode (stage, kind, chunk, local index).  A CTA's tasks increase, so
@@ -631,19 +631,17 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
       }
     }
     if (kind < 0) { kind = 2; c = st - 2 * a.lag; }
+    const int jv = c * a.B + local / (kind == 1 ? a.CG : a.RB);   // the task's view
 
-    // Wait for what this task consumes.
+    // Wait for what this task consumes (the producers of its own view).
     if (threadIdx.x == 0) {
       bool ok = true;
       if (kind == 0) {
-        if (c >= a.nslot) {
-          const int cp = c - a.nslot;
-          ok = spin_wait_geq(doneI + cp, min(a.B, a.J - cp * a.B) * a.RB, a.status);
-        }
+        if (c >= a.nslot) ok = spin_wait_geq(doneI + (jv - a.nslot * a.B), a.RB, a.status);
       } else if (kind == 1) {
-        ok = spin_wait_geq(doneR + c, min(a.B, a.J - c * a.B) * a.RB, a.status);
+        ok = spin_wait_geq(doneR + jv, a.RB, a.status);
       } else {
-        ok = spin_wait_geq(doneC + c, min(a.B, a.J - c * a.B) * a.CG, a.status);
+        ok = spin_wait_geq(doneC + jv, a.CG, a.status);
       }
       s_skip = ok ? 0 : 1;
     }
@@ -685,7 +683,7 @@ __device__ __forceinline__ void fourier_tasks(const FourierArgs* as, const CUten
     if (threadIdx.x == 0) {
       bulk_wait<0>();   // TMA stores of the task have landed
       __threadfence();
-      atomicAdd((kind == 0 ? doneR : kind == 1 ? doneC : doneI) + c, 1);
+      atomicAdd((kind == 0 ? doneR : kind == 1 ? doneC : doneI) + jv, 1);
     }
   }
   // Copies that a timed-out wait left in flight must land before the CTA exits.

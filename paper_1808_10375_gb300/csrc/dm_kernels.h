@@ -64,8 +64,7 @@ struct FourierArgs {
                           // every slot): G * M slots busy out of kThreads / (w R2)
   int nstages, total_tasks;
   const int* stage_off;   // [nstages + 1] first task of each stage
-  int* counters;          // [0] dispenser, then done R/C/I per view [J] (single-scan kernels)
-                          // or per chunk [nchunks] (the batched kernel)
+  int* counters;          // [0] dispenser, then done R/C/I per view [J]
   int* status;
 };
 
