@@ -1024,6 +1024,7 @@ def main():
         c2 = dm.dm_init(params, pos_h, inten_h, p0_h, o0_h, stream=stream.cuda_stream)
         if form_req is not None:
             dm.dm_set_fourier_form(c2, form_req)
+        dm.dm_set_graph(c2, True)   # as in the device-timed loop (the captures happen in this session)
         dm.dm_iterate(c2, args.steps)
         dm.dm_get_object(c2, out=o_out)
         dm.dm_get_probe(c2, out=p_out)
@@ -1036,8 +1037,9 @@ def main():
         d2h = o_out.numel() * 8 + p_out.numel() * 8 + 8 * (2 + m)
         e2e = {"value": job_throughput(world, j, m, args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-               "session": f"dm_init from pinned host buffers + {args.steps} iterations + object, probe "
-                          f"and metrics to host, per step = session / {args.steps}",
+               "session": f"dm_init from pinned host buffers + {args.steps} iterations (CUDA-graph replay, "
+                          f"captured in the session) + object, probe and metrics to host, per step = session / "
+                          f"{args.steps}",
                "fourier_plan": "default"}
 
     # ---- CPU oracle baseline (rank 0, N = 1) ---------------------------------
