@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--autotune", type=int, default=0, metavar="V",
                     help="pick the Fourier-step plan with dm_autotune on the first V views before timing (0: the "
                          "default plan)")
-    ap.add_argument("--form", choices=["auto", "strip", "split"], default="auto",
+    ap.add_argument("--form", choices=["auto", "strip", "split", "cluster"], default="auto",
                     help="Fourier-step form (auto: the context's choice, the split form for 256x256 frames with 8 "
                          "modes; after --autotune the autotuner's)")
     ap.add_argument("--psi", choices=["fp32", "fp16"], default="fp32",
@@ -191,8 +191,13 @@ def make_inputs(views, device, name=WORKLOAD):
     return s, p0.astype(np.complex64), o0.astype(np.complex64)
 
 
-FORM_KERNEL = {"strip": "dm_fourier.cu", "split": "dm_fourier_split.cu"}
+FORM_KERNEL = {"strip": "dm_fourier.cu", "split": "dm_fourier_split.cu", "cluster": "dm_fourier_cluster.cu"}
 FORM_TRAFFIC = {"strip": "fourier_mm256_traffic.json", "split": "fourier_split_mm256_traffic.json"}
+FORM_KERNEL_NAME = {
+    "strip": "k_fourier (persistent Fourier step, Eq. 3, strip form)",
+    "split": "k_fourier_split (persistent Fourier step, Eq. 3, split-column form)",
+    "cluster": "k_fourier_cluster (Fourier step, Eq. 3, one cluster per view, frames in shared memory)",
+}
 
 
 def kernel_source_hash(form="strip"):
@@ -210,6 +215,8 @@ def stored_traffic(views, form="strip"):
     """DRAM bytes of one Fourier-step launch of the given form from the
     committed ncu summary, scaled from its capture size to `views` views, or
     None if the kernel changed since the capture."""
+    if form not in FORM_TRAFFIC:
+        return None
     try:
         with open(os.path.join(ROOT, "profiles", FORM_TRAFFIC[form])) as f:
             d = json.load(f)
@@ -944,12 +951,13 @@ def main():
     torch.cuda.set_stream(stream)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     ctx = dm.dm_init(params, dev(s.pos), s.intensities, dev(p0), dev(o0), stream=stream.cuda_stream)
-    form_req = {"strip": dm.DM_FOURIER_STRIP, "split": dm.DM_FOURIER_SPLIT}.get(args.form)
+    form_req = {"strip": dm.DM_FOURIER_STRIP, "split": dm.DM_FOURIER_SPLIT,
+                "cluster": dm.DM_FOURIER_CLUSTER}.get(args.form)
     if form_req is not None:
         dm.dm_set_fourier_form(ctx, form_req)
     if args.autotune > 0:
         dm.dm_autotune(ctx, sample_views=min(j, args.autotune))
-    form = "split" if dm.dm_get_fourier_form(ctx) == dm.DM_FOURIER_SPLIT else "strip"
+    form = {dm.DM_FOURIER_SPLIT: "split", dm.DM_FOURIER_CLUSTER: "cluster"}.get(dm.dm_get_fourier_form(ctx), "strip")
     plan = dm.dm_get_plan(ctx)
     # iterations replay captured CUDA graphs (one per pair of current object and
     # probe buffers, captured during the warm-up)
@@ -992,8 +1000,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None,
                 "traffic": stored_traffic(j, form) if (wname == WORKLOAD and args.psi == "fp32") else None,
-                "kernel": ("k_fourier_split (persistent Fourier step, Eq. 3, split-column form)" if form == "split"
-                           else "k_fourier (persistent Fourier step, Eq. 3, strip form)"),
+                "kernel": FORM_KERNEL_NAME[form],
                 "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": f_bytes, "avg_launch_ms": f_ms / f_n if f_n else None,
                 "object_source_bytes_per_launch": c_bytes,

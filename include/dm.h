@@ -301,9 +301,19 @@ int dm_get_plan(const dm_ctx* ctx, int64_t* out);
  * dm_set_fourier_form selects one explicitly
  * (DM_EINVAL for DM_FOURIER_SPLIT on other shapes); it synchronises and
  * drops captured iteration graphs.  dm_get_fourier_form
- * reports the form the next Fourier step runs. */
+ * reports the form the next Fourier step runs.
+ * DM_FOURIER_CLUSTER (128 x 128 frames with 1 to 8 modes): one thread-block
+ * cluster per view and one CTA per mode; each CTA holds its mode's whole
+ * frame in shared memory and runs both 1-D passes of both transforms there,
+ * and the mode sums (S of the modulus projection, and c_j = sum_k conj(P_k)
+ * psi'_k of Eq. 5) are reduce-scatters over the cluster's distributed shared
+ * memory.  It has no scratch ring (dm_get_plan reports 0 bytes, 1 view per
+ * cluster, 0 strips and buffers, and its CTAs).  Like the split form it
+ * leaves the exit-wave change and batches to the strip form.  dm_autotune
+ * times it against the strip plans where it exists. */
 #define DM_FOURIER_STRIP 0
 #define DM_FOURIER_SPLIT 1
+#define DM_FOURIER_CLUSTER 2
 int dm_set_fourier_form(dm_ctx* ctx, int32_t form);
 int dm_get_fourier_form(const dm_ctx* ctx, int32_t* form);
 

@@ -115,6 +115,9 @@ struct dm_ctx {
   int fsgrid = 0;
   size_t fssmem = 0;
   CUtensorMap tmap_split[2];    // scratch rows (box 16 x 128, swizzled), intensities (box 16 x 16)
+  // the cluster form of the Fourier step (128 x 128 frames, 1 to 8 modes)
+  bool cluster_ok = false;      // the form exists for this scan
+  int ccap = 0;                 // clusters resident at once
   int ef_cg = 0;                // column tasks per view of the last Fourier launch (rows of ef_part)
   int probe_groups = 0;
   int probe_final_blocks = 0;
@@ -432,6 +435,7 @@ int encode_split_maps(dm_ctx* c, const dmk::FourierArgs& a, float2* scratch, CUt
 // Whether the next Fourier step runs the split form (the exit-wave change is
 // tracked by the strip form only).
 bool use_split(const dm_ctx* c) { return c->split_ok && c->form == DM_FOURIER_SPLIT && !c->psi_err; }
+bool use_cluster(const dm_ctx* c) { return c->cluster_ok && c->form == DM_FOURIER_CLUSTER && !c->psi_err; }
 
 // Plan the Fourier step of the whole scan with knobs `k` and allocate its
 // buffers (scratch ring, stage offsets, counters, Fourier-error partials).
@@ -556,6 +560,12 @@ int run_fourier(dm_ctx* c) {
   a.obj = c->obj[c->cur_O];
   a.psi = psi_cur(c);
   a.psi16 = c->half ? 1 : 0;
+  if (use_cluster(c)) {
+    c->ef_cg = c->M;   // one Fourier-error partial per view and mode
+    Timed t(c, DM_KERNEL_FOURIER);
+    DM_CUDA(c, dmk::launch_fourier_cluster(a, std::min(c->J, c->ccap), c->stream));
+    return DM_OK;
+  }
   c->ef_cg = a.CG;
   Timed t(c, DM_KERNEL_FOURIER);
   if (split) DM_CUDA(c, dmk::launch_fourier_split(c->tmap_split, a, c->fsgrid, c->fssmem, c->stream));
@@ -770,6 +780,10 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   // with its own ring size); dm_autotune may pick the other
   c->form = c->split_ok ? DM_FOURIER_SPLIT : DM_FOURIER_STRIP;
   if (c->split_ok) DM_TRY(alloc_n(c, &c->isplit, (size_t)J * nn));
+  if (N == dmk::kClusterN && M <= dmk::kClusterMaxModes) {
+    c->ccap = dmk::fourier_cluster_capacity(M);
+    c->cluster_ok = c->ccap > 0;
+  }
   DM_TRY(alloc_n(c, &c->probe[0], (size_t)M * nn));
   DM_TRY(alloc_n(c, &c->probe[1], (size_t)M * nn));
   DM_TRY(alloc_n(c, &c->obj[0], (size_t)c->H * c->W));
@@ -983,6 +997,7 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
     size_t smem;
     int grid;
     bool split;
+    bool cluster = false;
   };
   std::vector<Plan> plans;
   size_t max_scr = 0, max_off = 0, max_cnt = 0;
@@ -1008,6 +1023,18 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
           max_cnt = std::max(max_cnt, 1 + 3 * (size_t)Js);
           plans.push_back(std::move(pl));
         }
+  // the cluster form (no knobs) where the scan has it
+  if (c->cluster_ok && !c->psi_err) {
+    Plan pl;
+    pl.k = c->knobs;
+    pl.a = c->fa;
+    pl.a.J = Js;
+    pl.smem = 0;
+    pl.grid = std::min(Js, c->ccap);
+    pl.split = false;
+    pl.cluster = true;
+    plans.push_back(std::move(pl));
+  }
   float2 *scr = nullptr, *psi_save = nullptr;
   int *offd = nullptr, *cnt = nullptr;
   double* ef = nullptr;
@@ -1028,7 +1055,7 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
   cudaEvent_t e0 = take_event(c), e1 = take_event(c);
   double best = 1e300;
   FourierKnobs best_k = c->knobs;
-  bool best_split = use_split(c);
+  bool best_split = use_split(c), best_cluster = use_cluster(c);
   constexpr int kReps = 3;
   for (Plan& pl : plans) {
     dmk::FourierArgs a = pl.a;
@@ -1037,28 +1064,36 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
     a.tw = c->tw; a.stage_off = offd; a.counters = cnt; a.status = c->status;
     a.probe = c->probe[c->cur_P]; a.obj = c->obj[c->cur_O];
     CUtensorMap map[2];
-    if ((rc = pl.split ? encode_split_maps(c, a, scr, map) : encode_scratch_map(c, a, scr, map))) {
+    if (!pl.cluster && (rc = pl.split ? encode_split_maps(c, a, scr, map) : encode_scratch_map(c, a, scr, map))) {
       release();
       return rc;
     }
-    cudaError_t e = cudaMemcpyAsync(offd, pl.off.data(), pl.off.size() * sizeof(int), cudaMemcpyHostToDevice,
-                                    c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    // sets the kernel's shared-memory limit for this plan
-    if (pl.split) dmk::fourier_split_occupancy(pl.smem); else dmk::fourier_occupancy(N, pl.smem);
+    cudaError_t e = cudaSuccess;
+    if (!pl.cluster) {
+      e = cudaMemcpyAsync(offd, pl.off.data(), pl.off.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      // sets the kernel's shared-memory limit for this plan
+      if (pl.split) dmk::fourier_split_occupancy(pl.smem); else dmk::fourier_occupancy(N, pl.smem);
+    }
     for (int r = 0; r <= kReps && e == cudaSuccess; ++r) {   // the first run warms up
       if (r == 1) e = cudaEventRecord(e0, c->stream);
       if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + 3 * (size_t)Js), c->stream);
       if (e == cudaSuccess)
-        e = pl.split ? dmk::launch_fourier_split(map, a, pl.grid, pl.smem, c->stream)
-                     : dmk::launch_fourier(map, a, pl.grid, pl.smem, c->stream);
+        e = pl.cluster ? dmk::launch_fourier_cluster(a, pl.grid, c->stream)
+            : pl.split ? dmk::launch_fourier_split(map, a, pl.grid, pl.smem, c->stream)
+                       : dmk::launch_fourier(map, a, pl.grid, pl.smem, c->stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e != cudaSuccess) { release(); return cuda_fail(c, e, "autotune run"); }
-    if (ms / kReps < best) { best = ms / kReps; best_k = pl.k; best_split = pl.split; }
+    if (ms / kReps < best) {
+      best = ms / kReps;
+      best_k = pl.k;
+      best_split = pl.split;
+      best_cluster = pl.cluster;
+    }
   }
   c->event_pool.push_back(e0);
   c->event_pool.push_back(e1);
@@ -1075,13 +1110,21 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
     dev_free(c, q);
   c->scratch = nullptr; c->stage_off = nullptr; c->counters = nullptr; c->ef_part = nullptr; c->stage_off_s = nullptr;
   if ((rc = plan_fourier(c, best_k))) return rc;
-  if (c->split_ok) c->form = best_split ? DM_FOURIER_SPLIT : DM_FOURIER_STRIP;
+  c->form = best_cluster ? DM_FOURIER_CLUSTER : best_split ? DM_FOURIER_SPLIT : DM_FOURIER_STRIP;
   if (best_ms) *best_ms = best;
   return DM_OK;
 }
 
 int dm_get_plan(const dm_ctx* c, int64_t* out) {
   if (!c || !out) return DM_EINVAL;
+  if (use_cluster(c)) {   // no scratch ring: one view per cluster of M CTAs at a time
+    out[0] = 0;
+    out[1] = 1;
+    out[2] = 0;
+    out[3] = 0;
+    out[4] = (int64_t)std::min(c->J, c->ccap) * c->M;
+    return DM_OK;
+  }
   const bool split = use_split(c);
   const dmk::FourierArgs& a = split ? c->fs : c->fa;
   out[0] = (int64_t)scratch_elems(a) * (int64_t)sizeof(float2);
@@ -1095,9 +1138,12 @@ int dm_get_plan(const dm_ctx* c, int64_t* out) {
 int dm_set_fourier_form(dm_ctx* c, int32_t form) {
   int rc = check_ctx(c);
   if (rc) return rc;
-  if (form != DM_FOURIER_STRIP && form != DM_FOURIER_SPLIT) return fail(c, DM_EINVAL, "unknown Fourier form");
+  if (form != DM_FOURIER_STRIP && form != DM_FOURIER_SPLIT && form != DM_FOURIER_CLUSTER)
+    return fail(c, DM_EINVAL, "unknown Fourier form");
   if (form == DM_FOURIER_SPLIT && !c->split_ok)
     return fail(c, DM_EINVAL, "the split form needs 256 x 256 frames and 8 modes");
+  if (form == DM_FOURIER_CLUSTER && !c->cluster_ok)
+    return fail(c, DM_EINVAL, "the cluster form needs 128 x 128 frames and 1 to 8 modes");
   if (form == c->form) return DM_OK;
   DM_CUDA(c, cudaStreamSynchronize(c->stream));   // no captured iteration is in flight below
   c->form = form;
@@ -1110,7 +1156,7 @@ int dm_set_fourier_form(dm_ctx* c, int32_t form) {
 
 int dm_get_fourier_form(const dm_ctx* c, int32_t* form) {
   if (!c || c->magic != 0x58434D44u || !form) return DM_EINVAL;
-  *form = use_split(c) ? DM_FOURIER_SPLIT : DM_FOURIER_STRIP;
+  *form = use_cluster(c) ? DM_FOURIER_CLUSTER : use_split(c) ? DM_FOURIER_SPLIT : DM_FOURIER_STRIP;
   return DM_OK;
 }
 

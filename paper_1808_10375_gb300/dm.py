@@ -26,7 +26,7 @@ DM_STEP_FOURIER, DM_STEP_OBJECT, DM_STEP_PROBE = 0, 1, 2
 DM_DFT_FP32, DM_DFT_BF16X3, DM_DFT_BF16X3_TC05 = 0, 1, 2
 DM_ORDER_GAUSS_SEIDEL, DM_ORDER_JACOBI = 0, 1
 DM_PSI_FP32, DM_PSI_FP16 = 0, 1
-DM_FOURIER_STRIP, DM_FOURIER_SPLIT = 0, 1
+DM_FOURIER_STRIP, DM_FOURIER_SPLIT, DM_FOURIER_CLUSTER = 0, 1, 2
 DM_NET_LOSS_MSE, DM_NET_LOSS_GAUGE = 0, 1
 (DM_KERNEL_FOURIER, DM_KERNEL_OBJECT_GATHER, DM_KERNEL_OBJECT_FINAL, DM_KERNEL_PROBE_PARTIAL,
  DM_KERNEL_PROBE_FINAL, DM_KERNEL_METRICS, DM_KERNEL_OTHER, DM_KERNEL_COUNT) = range(8)
@@ -628,12 +628,12 @@ def dm_get_psi_precision(ctx: Context):
 
 
 def dm_set_fourier_form(ctx: Context, form: int):
-    """Run the Fourier step in DM_FOURIER_STRIP or DM_FOURIER_SPLIT form (see dm.h)."""
+    """Run the Fourier step in DM_FOURIER_STRIP, DM_FOURIER_SPLIT or DM_FOURIER_CLUSTER form (see dm.h)."""
     return _check(load().dm_set_fourier_form(ctx.handle, int(form)), ctx)
 
 
 def dm_get_fourier_form(ctx: Context) -> int:
-    """The form the next Fourier step runs (DM_FOURIER_STRIP or DM_FOURIER_SPLIT)."""
+    """The form the next Fourier step runs (DM_FOURIER_STRIP, DM_FOURIER_SPLIT or DM_FOURIER_CLUSTER)."""
     form = ctypes.c_int32()
     _check(load().dm_get_fourier_form(ctx.handle, ctypes.byref(form)), ctx)
     return form.value
