@@ -309,8 +309,11 @@ int dm_get_plan(const dm_ctx* ctx, int64_t* out);
  * psi'_k of Eq. 5) are reduce-scatters over the cluster's distributed shared
  * memory.  It has no scratch ring (dm_get_plan reports 0 bytes, 1 view per
  * cluster, 0 strips and buffers, and its CTAs).  Like the split form it
- * leaves the exit-wave change and batches to the strip form.  dm_autotune
- * times it against the strip plans where it exists. */
+ * leaves the exit-wave change and batches to the strip form.  Contexts that
+ * have it start in it when the scan has at most three views per cluster
+ * that fits the GPU at once (it is the faster form of short scans, whose
+ * strip pipeline cannot fill); dm_autotune times it against the strip plans
+ * where it exists. */
 #define DM_FOURIER_STRIP 0
 #define DM_FOURIER_SPLIT 1
 #define DM_FOURIER_CLUSTER 2

@@ -51,6 +51,7 @@ def test_batch_equals_scans_alone(graph):
     cases = [case(*spec[:5], spec[5]) for spec in SCANS]
     alone = _contexts(cases)
     for c in alone:
+        dm.dm_set_fourier_form(c, dm.DM_FOURIER_STRIP)   # the form the batch runs
         dm.dm_iterate(c, 3)
     ref = [_state(c) for c in alone]
     for c in alone:

@@ -93,6 +93,8 @@ def test_cluster_form_selection_rules():
     h, w = s.obj_shape
     params = dm.dm_params_default(n=128, modes=4, views=s.views, obj_h=h, obj_w=w)
     ctx = dm.dm_init(params, s.pos, s.intensities, p0, o0)
+    assert dm.dm_get_fourier_form(ctx) == dm.DM_FOURIER_CLUSTER   # a short scan starts in it
+    dm.dm_set_fourier_form(ctx, dm.DM_FOURIER_STRIP)
     dm.dm_set_fourier_form(ctx, dm.DM_FOURIER_CLUSTER)
     assert dm.dm_get_fourier_form(ctx) == dm.DM_FOURIER_CLUSTER
     plan = dm.dm_get_plan(ctx)
@@ -102,6 +104,14 @@ def test_cluster_form_selection_rules():
     dm.dm_set_psi_error(ctx, 0)
     assert dm.dm_get_fourier_form(ctx) == dm.DM_FOURIER_CLUSTER
     dm.dm_set_fourier_form(ctx, dm.DM_FOURIER_STRIP)
+    assert dm.dm_get_fourier_form(ctx) == dm.DM_FOURIER_STRIP
+    dm.dm_free(ctx)
+    # a long scan (400 views: more than three per resident cluster) starts in
+    # the strip form
+    s, p0, o0, psi0 = case(128, 4, (20, 20), 8, (285, 285), 51, probe="hg", noise=False)
+    h, w = s.obj_shape
+    params = dm.dm_params_default(n=128, modes=4, views=s.views, obj_h=h, obj_w=w)
+    ctx = dm.dm_init(params, s.pos, s.intensities, p0, o0)
     assert dm.dm_get_fourier_form(ctx) == dm.DM_FOURIER_STRIP
     dm.dm_free(ctx)
 

@@ -71,8 +71,10 @@ def test_contexts_of_one_frame_size_with_different_plans():
         params = dm.dm_params_default(n=s.n, modes=s.modes, views=s.views, obj_h=h, obj_w=w)
         c = dm.dm_init(params, s.pos, s.intensities, p0, o0)
         dm.dm_set_exit_waves(c, psi0)
+        dm.dm_set_fourier_form(c, dm.DM_FOURIER_STRIP)   # the form whose plans differ in shared memory
         ctxs.append(c)
     dm.dm_autotune(ctxs[1], sample_views=9)
+    dm.dm_set_fourier_form(ctxs[1], dm.DM_FOURIER_STRIP)
     for c in ctxs:
         dm.dm_iterate(c, 1)
     for c, (s, p0, o0, psi0) in zip(ctxs, (big, small)):
