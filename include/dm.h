@@ -265,9 +265,11 @@ int dm_set_graph(dm_ctx* ctx, int32_t enable);
  * sample_views views of the context (one warm-up and three timed runs of the
  * Fourier kernel each); where the scan has the split form (and the exit-wave
  * change is not tracked), that form is timed too at each ring size (48 to
- * 192 MiB), so the choice covers the form as well (dm_get_fourier_form
- * reports it).  The
- * fastest is kept for the whole scan.  The exit
+ * 192 MiB), and so is the cluster form where the scan has it, so the choice
+ * covers the form as well (dm_get_fourier_form reports it).  The fastest
+ * form is kept for the whole scan, and so is the fastest plan of each form
+ * (a batch or the exit-wave change runs the strip form with its best
+ * plan whichever form won).  The exit
  * waves of the sample views are restored afterwards; the object sources are
  * recomputed by the next iteration, so results are unchanged.  Temporary
  * buffers (up to the largest ring plus a copy of the sample's exit waves)
@@ -309,7 +311,8 @@ int dm_get_plan(const dm_ctx* ctx, int64_t* out);
  * psi'_k of Eq. 5) are reduce-scatters over the cluster's distributed shared
  * memory.  It has no scratch ring (dm_get_plan reports 0 bytes, 1 view per
  * cluster, 0 strips and buffers, and its CTAs).  Like the split form it
- * leaves the exit-wave change and batches to the strip form.  Contexts that
+ * leaves the exit-wave change to the strip form; in a dm_batch a scan in the
+ * cluster form keeps it (a launch of its own).  Contexts that
  * have it start in it when the scan has at most three views per cluster
  * that fits the GPU at once (it is the faster form of short scans, whose
  * strip pipeline cannot fill); dm_autotune times it against the strip plans
@@ -324,8 +327,11 @@ int dm_get_fourier_form(const dm_ctx* ctx, int32_t* form);
  * device; any frame sizes, mode and view counts) keep their own data and
  * plans; an iteration of the batch runs, for each frame size, one persistent
  * Fourier-step launch over all scans of that size (up to 16 per launch; more
- * scans take further launches), then each scan's object and probe updates
- * and metrics.  Each scan's results equal those of dm_iterate on it alone.
+ * scans take further launches) in the strip form -- scans in the cluster form
+ * take a cluster launch of their own instead -- then each scan's object and
+ * probe updates and metrics.  Each scan's results equal those of dm_iterate
+ * on it alone in the same form (the strip form for a scan whose own is the
+ * split form).
  * The work runs on a stream the batch owns, ordered after the work queued on
  * every context's stream and before work queued on them afterwards.
  * dm_batch_set_graph(b, 1) captures a batch iteration as one CUDA graph per

@@ -1060,6 +1060,11 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
   double best = 1e300;
   FourierKnobs best_k = c->knobs;
   bool best_split = use_split(c), best_cluster = use_cluster(c);
+  // the best plan of each form is kept as well: batches and the exit-wave
+  // change run the strip form whichever form wins
+  double best_strip_t = 1e300, best_split_t = 1e300;
+  FourierKnobs strip_k = c->knobs;
+  size_t split_budget = c->knobs.split_budget;
   constexpr int kReps = 3;
   for (Plan& pl : plans) {
     dmk::FourierArgs a = pl.a;
@@ -1092,9 +1097,11 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e != cudaSuccess) { release(); return cuda_fail(c, e, "autotune run"); }
-    if (ms / kReps < best) {
-      best = ms / kReps;
-      best_k = pl.k;
+    const double t = ms / kReps;
+    if (!pl.split && !pl.cluster && t < best_strip_t) { best_strip_t = t; strip_k = pl.k; }
+    if (pl.split && t < best_split_t) { best_split_t = t; split_budget = pl.k.split_budget; }
+    if (t < best) {
+      best = t;
       best_split = pl.split;
       best_cluster = pl.cluster;
     }
@@ -1113,6 +1120,8 @@ int dm_autotune(dm_ctx* c, int32_t sample_views, double* best_ms) {
   for (void* q : {(void*)c->scratch, (void*)c->stage_off, (void*)c->counters, (void*)c->ef_part, (void*)c->stage_off_s})
     dev_free(c, q);
   c->scratch = nullptr; c->stage_off = nullptr; c->counters = nullptr; c->ef_part = nullptr; c->stage_off_s = nullptr;
+  best_k = strip_k;
+  best_k.split_budget = split_budget;
   if ((rc = plan_fourier(c, best_k))) return rc;
   c->form = best_cluster ? DM_FOURIER_CLUSTER : best_split ? DM_FOURIER_SPLIT : DM_FOURIER_STRIP;
   if (best_ms) *best_ms = best;
@@ -1213,21 +1222,32 @@ int enqueue_batch_iteration(dm_batch* b) {
   for (size_t gi = 0; gi < b->groups.size(); ++gi) {
     auto& g = b->groups[gi];
     dmk::FourierBatch fb{};
-    fb.nscan = (int)g.scans.size();
     fb.dispenser = b->dispensers + gi;
-    int base = 0;
-    for (int s = 0; s < fb.nscan; ++s) {
-      dm_ctx* c = b->ctx[g.scans[s]];
+    int base = 0, ns = 0;
+    for (int scan : g.scans) {
+      dm_ctx* c = b->ctx[scan];
       c->fa.probe = c->probe[c->cur_P];
       c->fa.obj = c->obj[c->cur_O];
-      fb.a[s] = c->fa;
-      fb.map[s] = c->tmap_s[0];
-      c->ef_cg = c->fa.CG;   // the batched launch runs the strip form
-      fb.base[s] = base;
+      c->fa.psi = psi_cur(c);
+      c->fa.psi16 = c->half ? 1 : 0;
+      if (use_cluster(c)) {
+        // a scan in the cluster form keeps it: a launch of its own (one view
+        // per cluster, nothing to share with the persistent launch)
+        c->ef_cg = c->M;
+        DM_BCUDA(b, dmk::launch_fourier_cluster(c->fa, std::min(c->J, c->ccap), b->stream));
+        continue;
+      }
+      fb.a[ns] = c->fa;
+      fb.map[ns] = c->tmap_s[0];
+      c->ef_cg = c->fa.CG;   // the persistent launch runs the strip form
+      fb.base[ns] = base;
       base += c->fa.total_tasks;
       DM_BCUDA(b, cudaMemsetAsync(c->counters, 0, c->counters_bytes, b->stream));
+      ++ns;
     }
-    fb.base[fb.nscan] = base;
+    if (ns == 0) continue;
+    fb.nscan = ns;
+    fb.base[ns] = base;
     DM_BCUDA(b, cudaMemsetAsync(fb.dispenser, 0, sizeof(int), b->stream));
     DM_BCUDA(b, dmk::launch_fourier_batch(fb, g.N, g.grid, g.smem, b->stream));
   }
@@ -1249,7 +1269,7 @@ int enqueue_batch_iteration(dm_batch* b) {
       if (!upd) break;
       if (rc == DM_OK) rc = run_probe(c, probe_object(c));
     }
-    if (rc == DM_OK) rc = run_metrics(c, c->ef_part, (long long)c->J * c->fa.CG, c->isum, upd, false);
+    if (rc == DM_OK) rc = run_metrics(c, c->ef_part, (long long)c->J * c->ef_cg, c->isum, upd, false);
     c->stream = own;
     if (rc) return batch_fail(b, rc, c->err);
     DM_BCUDA(b, cudaEventRecord(b->joins[i], b->lanes[i]));
@@ -1330,7 +1350,7 @@ int dm_batch_iterate(dm_batch* b, int32_t n_iter) {
     std::vector<int> key;
     for (dm_ctx* c : b->ctx) {
       graph_ok = graph_ok && !c->timing && c->iters >= c->p.probe_update_start;
-      key.push_back(c->cur_O * 2 + c->cur_P);
+      key.push_back(c->cur_O * 2 + c->cur_P + (use_cluster(c) ? 4 : 0));   // buffers and form
     }
     if (graph_ok) {
       cudaGraphExec_t g = nullptr;
