@@ -312,10 +312,10 @@ int dm_get_plan(const dm_ctx* ctx, int64_t* out);
  * memory.  It has no scratch ring (dm_get_plan reports 0 bytes, 1 view per
  * cluster, 0 strips and buffers, and its CTAs).  Like the split form it
  * leaves the exit-wave change to the strip form; in a dm_batch a scan in the
- * cluster form keeps it (a launch of its own).  Contexts that
- * have it start in it when the scan has at most three views per cluster
- * that fits the GPU at once (it is the faster form of short scans, whose
- * strip pipeline cannot fill); dm_autotune times it against the strip plans
+ * cluster form keeps it (a launch of its own).  Contexts that have it start
+ * in it with one or two modes, and with more when the scan has at most three
+ * views per cluster that fits the GPU at once (the strip pipeline of such a
+ * short scan cannot fill); dm_autotune times it against the strip plans
  * where it exists. */
 #define DM_FOURIER_STRIP 0
 #define DM_FOURIER_SPLIT 1

@@ -783,10 +783,12 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   if (N == dmk::kClusterN && M <= dmk::kClusterMaxModes) {
     c->ccap = dmk::fourier_cluster_capacity(M);
     c->cluster_ok = c->ccap > 0;
-    // the cluster form for scans of at most three views per resident cluster
-    // (measured on the 4-mode 128 x 128 scan: 0.096 against 0.109 ms per
-    // Fourier step at 108 views, even at 144, behind beyond)
-    if (c->cluster_ok && J <= 3 * c->ccap) c->form = DM_FOURIER_CLUSTER;
+    // the cluster form for one or two modes, and for scans of at most three
+    // views per resident cluster (Fourier step, ms, strip against cluster:
+    // 1 mode 1.02 / 0.54 and 2 modes 1.06 / 0.98 at 2,500 views; 4 modes
+    // 0.109 / 0.096 at 108 views, even at 144, 1.77 / 2.07 at 2,500; 3 and
+    // 8 modes behind at 576 views and more)
+    if (c->cluster_ok && (M <= 2 || J <= 3 * c->ccap)) c->form = DM_FOURIER_CLUSTER;
   }
   DM_TRY(alloc_n(c, &c->probe[0], (size_t)M * nn));
   DM_TRY(alloc_n(c, &c->probe[1], (size_t)M * nn));

@@ -107,13 +107,14 @@ def test_cluster_form_selection_rules():
     assert dm.dm_get_fourier_form(ctx) == dm.DM_FOURIER_STRIP
     dm.dm_free(ctx)
     # a long scan (400 views: more than three per resident cluster) starts in
-    # the strip form
-    s, p0, o0, psi0 = case(128, 4, (20, 20), 8, (285, 285), 51, probe="hg", noise=False)
-    h, w = s.obj_shape
-    params = dm.dm_params_default(n=128, modes=4, views=s.views, obj_h=h, obj_w=w)
-    ctx = dm.dm_init(params, s.pos, s.intensities, p0, o0)
-    assert dm.dm_get_fourier_form(ctx) == dm.DM_FOURIER_STRIP
-    dm.dm_free(ctx)
+    # the strip form with 4 modes, in the cluster form with 1 or 2
+    for m, want in ((4, dm.DM_FOURIER_STRIP), (2, dm.DM_FOURIER_CLUSTER), (1, dm.DM_FOURIER_CLUSTER)):
+        s, p0, o0, psi0 = case(128, m, (20, 20), 8, (285, 285), 51, probe="hg", noise=False)
+        h, w = s.obj_shape
+        params = dm.dm_params_default(n=128, modes=m, views=s.views, obj_h=h, obj_w=w)
+        ctx = dm.dm_init(params, s.pos, s.intensities, p0, o0)
+        assert dm.dm_get_fourier_form(ctx) == want, m
+        dm.dm_free(ctx)
 
 
 def test_cluster_form_complex_half_within_the_mixed_bounds():
