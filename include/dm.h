@@ -304,7 +304,7 @@ int dm_get_plan(const dm_ctx* ctx, int64_t* out);
  * (DM_EINVAL for DM_FOURIER_SPLIT on other shapes); it synchronises and
  * drops captured iteration graphs.  dm_get_fourier_form
  * reports the form the next Fourier step runs.
- * DM_FOURIER_CLUSTER (128 x 128 frames with 1 to 8 modes): one thread-block
+ * DM_FOURIER_CLUSTER (64 x 64 or 128 x 128 frames with 1 to 8 modes): one thread-block
  * cluster per view and one CTA per mode; each CTA holds its mode's whole
  * frame in shared memory and runs both 1-D passes of both transforms there,
  * and the mode sums (S of the modulus projection, and c_j = sum_k conj(P_k)
@@ -313,10 +313,10 @@ int dm_get_plan(const dm_ctx* ctx, int64_t* out);
  * cluster, 0 strips and buffers, and its CTAs).  Like the split form it
  * leaves the exit-wave change to the strip form; in a dm_batch a scan in the
  * cluster form keeps it (a launch of its own).  Contexts that have it start
- * in it with one or two modes, and with more when the scan has at most three
- * views per cluster that fits the GPU at once (the strip pipeline of such a
- * short scan cannot fill); dm_autotune times it against the strip plans
- * where it exists. */
+ * in it with up to two modes at 128 x 128 and up to four at 64 x 64, and
+ * with more when the scan has at most three views per cluster that fits the
+ * GPU at once (the strip pipeline of such a short scan cannot fill);
+ * dm_autotune times it against the strip plans where it exists. */
 #define DM_FOURIER_STRIP 0
 #define DM_FOURIER_SPLIT 1
 #define DM_FOURIER_CLUSTER 2

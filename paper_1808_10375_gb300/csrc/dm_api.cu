@@ -780,15 +780,18 @@ int dm_init(dm_ctx** out, const dm_params* p, const int32_t* positions, const fl
   // with its own ring size); dm_autotune may pick the other
   c->form = c->split_ok ? DM_FOURIER_SPLIT : DM_FOURIER_STRIP;
   if (c->split_ok) DM_TRY(alloc_n(c, &c->isplit, (size_t)J * nn));
-  if (N == dmk::kClusterN && M <= dmk::kClusterMaxModes) {
-    c->ccap = dmk::fourier_cluster_capacity(M);
+  if (dmk::fourier_cluster_shape(N, M)) {
+    c->ccap = dmk::fourier_cluster_capacity(N, M);
     c->cluster_ok = c->ccap > 0;
-    // the cluster form for one or two modes, and for scans of at most three
-    // views per resident cluster (Fourier step, ms, strip against cluster:
-    // 1 mode 1.02 / 0.54 and 2 modes 1.06 / 0.98 at 2,500 views; 4 modes
-    // 0.109 / 0.096 at 108 views, even at 144, 1.77 / 2.07 at 2,500; 3 and
-    // 8 modes behind at 576 views and more)
-    if (c->cluster_ok && (M <= 2 || J <= 3 * c->ccap)) c->form = DM_FOURIER_CLUSTER;
+    // the cluster form for up to two modes at 128 x 128 and up to four at
+    // 64 x 64, and for scans of at most three views per resident cluster
+    // (Fourier step, ms, strip against cluster, at 2,500 views: 128 x 128
+    // with 1 mode 1.02 / 0.54, 2 modes 1.06 / 0.98, 3 modes 1.50 / 1.65,
+    // 4 modes 1.77 / 2.07 (0.109 / 0.096 at 108 views, even at 144); 64 x 64
+    // with 1 mode 0.215 / 0.113, 4 modes 0.476 / 0.447, 8 modes 0.862 /
+    // 1.007 (0.074 / 0.046 at 100 views))
+    const int any_length = N == 64 ? 4 : 2;
+    if (c->cluster_ok && (M <= any_length || J <= 3 * c->ccap)) c->form = DM_FOURIER_CLUSTER;
   }
   DM_TRY(alloc_n(c, &c->probe[0], (size_t)M * nn));
   DM_TRY(alloc_n(c, &c->probe[1], (size_t)M * nn));
@@ -1158,7 +1161,7 @@ int dm_set_fourier_form(dm_ctx* c, int32_t form) {
   if (form == DM_FOURIER_SPLIT && !c->split_ok)
     return fail(c, DM_EINVAL, "the split form needs 256 x 256 frames and 8 modes");
   if (form == DM_FOURIER_CLUSTER && !c->cluster_ok)
-    return fail(c, DM_EINVAL, "the cluster form needs 128 x 128 frames and 1 to 8 modes");
+    return fail(c, DM_EINVAL, "the cluster form needs 64 x 64 or 128 x 128 frames and 1 to 8 modes");
   if (form == c->form) return DM_OK;
   DM_CUDA(c, cudaStreamSynchronize(c->stream));   // no captured iteration is in flight below
   c->form = form;
@@ -1197,6 +1200,7 @@ struct dm_batch {
   // the scans' overlap projections run concurrently, one stream per scan,
   // forked after the Fourier launches and joined before the iteration ends
   std::vector<cudaStream_t> lanes;
+  cudaEvent_t begin = nullptr;   // start of an iteration: the cluster-form scans' lanes fork here
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> joins;
   bool use_graph = false;
@@ -1221,6 +1225,7 @@ int batch_fail(dm_batch* b, int code, const std::string& msg) {
 
 // Every launch of one batch iteration on the batch's stream.
 int enqueue_batch_iteration(dm_batch* b) {
+  DM_BCUDA(b, cudaEventRecord(b->begin, b->stream));
   for (size_t gi = 0; gi < b->groups.size(); ++gi) {
     auto& g = b->groups[gi];
     dmk::FourierBatch fb{};
@@ -1233,10 +1238,12 @@ int enqueue_batch_iteration(dm_batch* b) {
       c->fa.psi = psi_cur(c);
       c->fa.psi16 = c->half ? 1 : 0;
       if (use_cluster(c)) {
-        // a scan in the cluster form keeps it: a launch of its own (one view
-        // per cluster, nothing to share with the persistent launch)
+        // a scan in the cluster form keeps it: a launch of its own on the
+        // scan's lane, concurrent with the other scans' launches (its overlap
+        // projections follow on the same lane)
         c->ef_cg = c->M;
-        DM_BCUDA(b, dmk::launch_fourier_cluster(c->fa, std::min(c->J, c->ccap), b->stream));
+        DM_BCUDA(b, cudaStreamWaitEvent(b->lanes[scan], b->begin, 0));
+        DM_BCUDA(b, dmk::launch_fourier_cluster(c->fa, std::min(c->J, c->ccap), b->lanes[scan]));
         continue;
       }
       fb.a[ns] = c->fa;
@@ -1258,7 +1265,8 @@ int enqueue_batch_iteration(dm_batch* b) {
     dm_ctx* c = b->ctx[i];
     const bool upd = c->iters >= c->p.probe_update_start;
     cudaStream_t own = c->stream;
-    DM_BCUDA(b, cudaStreamWaitEvent(b->lanes[i], b->fork, 0));
+    // the strip-form scans follow the persistent launches
+    if (!use_cluster(c)) DM_BCUDA(b, cudaStreamWaitEvent(b->lanes[i], b->fork, 0));
     c->stream = b->lanes[i];
     int rc = DM_OK;
     for (int pass = 0; pass < c->p.n_inner && rc == DM_OK; ++pass) {
@@ -1323,6 +1331,7 @@ int dm_batch_create(dm_batch** out, dm_ctx* const* ctxs, int32_t count) {
   cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->begin, cudaEventDisableTiming);
   b->lanes.assign(b->ctx.size(), nullptr);
   b->joins.assign(b->ctx.size(), nullptr);
   for (size_t i = 0; i < b->ctx.size() && e == cudaSuccess; ++i) {
@@ -1404,6 +1413,7 @@ void dm_batch_free(dm_batch* b) {
     if (b->joins[i]) cudaEventDestroy(b->joins[i]);
   }
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->begin) cudaEventDestroy(b->begin);
   if (b->dispensers) cudaFreeAsync(b->dispensers, b->stream);
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->ev) cudaEventDestroy(b->ev);

@@ -1,8 +1,8 @@
 // Cluster form of the Fourier step (Eq. 3 with the constrained transform F_c
-// of Sec. II) for 128 x 128 frames and at most 8 modes.
+// of Sec. II) for 64 x 64 and 128 x 128 frames and at most 8 modes.
 //
 // One thread-block cluster per view and one CTA per mode: CTA k keeps the
-// whole frame of mode k in shared memory (128 KB of complex64), so both 1-D
+// whole frame of mode k in shared memory (32 or 128 KB of complex64), so both 1-D
 // passes of each 2-D DFT run out of shared memory and no intermediate goes
 // through global memory.  The two sums over the modes that couple the CTAs
 // -- S = sum_k |X_k|^2 of the modulus projection and the object source
@@ -42,34 +42,45 @@
 namespace dmk {
 namespace {
 
-constexpr int kCN = kClusterN;                 // frame side
-constexpr int kCT = 512;                       // threads per CTA
-constexpr int kCGroups = kCT / 8;              // 8-lane transform groups (64)
-constexpr int kCPix = kCN * kCN;
-static_assert(FftShape<kCN>::R1 == 16 && FftShape<kCN>::R2 == 8, "the layouts below assume 128 = 16 x 8");
-static_assert(kCN == 2 * kCGroups, "each group takes two lines per pass");
-constexpr size_t kFrameBytes = sizeof(float2) * kCPix;     // 128 KB
-constexpr size_t kNormBytes = sizeof(float) * kCPix;       // 64 KB
-constexpr size_t kTwCBytes = sizeof(float2) * kCN;         // W_128^(t k1), t < 8, k1 < 16
+// Shape of the kernel for frame side N: a 128-point line is 16 values x 8
+// lanes (two radix stages), a 64-point line 8 x 8; each 8-lane group takes
+// two lines per pass (512 threads for N = 128, 256 for N = 64).
+template <int N>
+struct CShape {
+  static constexpr int kT = N == 128 ? 512 : 256;          // threads per CTA
+  static constexpr int kGroups = kT / 8;                    // 8-lane transform groups
+  static constexpr int kR1 = FftShape<N>::R1;               // values per lane
+  static constexpr int kD = kR1 / 8;                        // pass-2 transforms per lane
+  static constexpr int kPix = N * N;
+  static constexpr size_t kFrameBytes = sizeof(float2) * kPix;   // 128 or 32 KB
+  static constexpr size_t kNormBytes = sizeof(float) * kPix;     // 64 or 16 KB
+  static constexpr size_t kTwBytes = sizeof(float2) * N;         // W_N^(t k1), t < 8, k1 < R1
+  static constexpr int kMinBlocks = N == 128 ? 1 : 3;            // CTAs per SM the registers allow
+  static_assert(FftShape<N>::R2 == 8 && (kR1 == 16 || kR1 == 8), "8-lane lines of 64 or 128 points");
+  static_assert(N == 2 * kGroups, "each group takes two lines per pass");
+};
 
-// Frame position (row r, column x) as a float2 index: 8 blocks of 16 columns,
-// each [128 rows][16 complex] with the row's 16-byte pairs permuted by
+// Frame position (row r, column x) as a float2 index: N/16 blocks of 16
+// columns, each [N rows][16 complex] with the row's 16-byte pairs permuted by
 // pair ^= r & 7.  A half-warp then touches 16 distinct 8-byte bank pairs for
 //   - 8 consecutive columns of rows r and r ^ 4 (row passes), and
 //   - 8 rows with distinct r & 7 of columns c and c ^ 1 (column passes).
+template <int N>
 __device__ __forceinline__ int fidx(int r, int x) {
-  return ((x >> 4) << 11) + (r << 4) + (((((x & 15) >> 1) ^ (r & 7)) << 1) | (x & 1));
+  return (x >> 4) * (N * 16) + (r << 4) + (((((x & 15) >> 1) ^ (r & 7)) << 1) | (x & 1));
 }
 
 // Norm-buffer position of pixel (row q, column x), in the strip order of the
 // intensities (strip s = x / 2: [s][q][x & 1]), the 32-word halves of odd
 // strips swapped so that the two strips of a column pass's half-warp fall on
 // different banks.
+template <int N>
 __device__ __forceinline__ int nidx_strip(int p) {   // p: pixel in strip order
-  const int s = p >> 8;
-  return (s << 8) + ((p & 255) ^ ((s & 1) << 4));
+  const int s = p / (2 * N);
+  return s * (2 * N) + ((p % (2 * N)) ^ ((s & 1) << 4));
 }
-__device__ __forceinline__ int nidx(int q, int x) { return nidx_strip(((x >> 1) << 8) + (q << 1) + (x & 1)); }
+template <int N>
+__device__ __forceinline__ int nidx(int q, int x) { return nidx_strip<N>((x >> 1) * (2 * N) + (q << 1) + (x & 1)); }
 
 // Exchange slot, along the transformed line, of pass-1 output k1 of lane t.
 // For fixed k1 the 8 lanes write 8 consecutive slots; for fixed (k1 group,
@@ -132,41 +143,49 @@ __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// One 128-point DFT along a line of the frame by the 8 lanes of a group:
-// v[i] = x[t + 8 i] on entry; on return X[t + 8 d + 16 k2] sits at
+// One N-point DFT along a line of the frame by the 8 lanes of a group:
+// v[i] = x[t + 8 i] on entry; on return X[t + 8 d + R1 k2] sits at
 // v[p2_index(d, k2)].  `at(pos)` is the frame index of line position pos.
 // The line is overwritten by the exchange; the first __syncwarp makes sure
 // every lane has read its inputs from the line first.
-template <bool INV, class At>
-__device__ __forceinline__ void line_dft(float2 (&v)[16], int t, const float2* tw, float2* F, At at) {
-  fft_pass1<kCN, INV>(v, t, tw);
+template <int N, bool INV, class At>
+__device__ __forceinline__ void line_dft(float2 (&v)[CShape<N>::kR1], int t, const float2* tw, float2* F, At at) {
+  using C = CShape<N>;
+  fft_pass1<N, INV>(v, t, tw);
   __syncwarp();
 #pragma unroll
-  for (int k1 = 0; k1 < 16; ++k1) F[at(xslot(k1, t))] = v[p1_index<kCN>(k1)];
+  for (int k1 = 0; k1 < C::kR1; ++k1) F[at(xslot(k1, t))] = v[p1_index<N>(k1)];
   __syncwarp();
 #pragma unroll
-  for (int d = 0; d < 2; ++d)
+  for (int d = 0; d < C::kD; ++d)
 #pragma unroll
     for (int tt = 0; tt < 8; ++tt) v[d * 8 + tt] = F[at(xslot(t + 8 * d, tt))];
   __syncwarp();
-  fft_pass2<kCN, INV>(v);
+  fft_pass2<N, INV>(v);
 }
 
-template <class PsiT>
-__global__ void __launch_bounds__(kCT, 1) k_fourier_cluster(const __grid_constant__ FourierArgs a) {
+// Line position of output (d, k2) of lane t after line_dft.
+template <int N>
+__device__ __forceinline__ int out_pos(int t, int d, int k2) { return t + 8 * d + CShape<N>::kR1 * k2; }
+
+template <int N, class PsiT>
+__global__ void __launch_bounds__(CShape<N>::kT, CShape<N>::kMinBlocks)
+    k_fourier_cluster(const __grid_constant__ FourierArgs a) {
+  using C = CShape<N>;
+  constexpr int kCT = C::kT, kCGroups = C::kGroups, kCPix = C::kPix, kR1 = C::kR1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* F = reinterpret_cast<float2*>(smem_raw);
-  float* NB = reinterpret_cast<float*>(smem_raw + kFrameBytes);
-  float2* tw = reinterpret_cast<float2*>(smem_raw + kFrameBytes + kNormBytes);
+  float* NB = reinterpret_cast<float*>(smem_raw + C::kFrameBytes);
+  float2* tw = reinterpret_cast<float2*>(smem_raw + C::kFrameBytes + C::kNormBytes);
   __shared__ double s_red[kCT / 32];
 
   const int tid = threadIdx.x, g = tid >> 3, t = tid & 7;
   const int M = a.M;
   const int r = (int)cluster_rank();         // this CTA's mode
   const float beta = a.beta, c2b = 2.f - beta;
-  const float invN = 1.f / (float)kCN, invN2 = invN * invN;
+  const float invN = 1.f / (float)N, invN2 = invN * invN;
   const uint32_t f_s = smem_u32(F), nb_s = smem_u32(NB);
-  for (int i = tid; i < kCN; i += kCT) tw[i] = a.tw[i];
+  for (int i = tid; i < N; i += kCT) tw[i] = a.tw[i];
   __syncthreads();
 
   // this CTA's share of the pixels in steps 3 (strip order, in fours) and 6
@@ -183,22 +202,22 @@ __global__ void __launch_bounds__(kCT, 1) k_fourier_cluster(const __grid_constan
 #pragma unroll 1
     for (int rho = 0; rho < 2; ++rho) {
       const int y = group_row(g) + kCGroups * rho;
-      const float2* prow = P_k + (size_t)y * kCN;
+      const float2* prow = P_k + (size_t)y * N;
       const float2* orow = a.obj + (size_t)(pos.x + y) * a.W + pos.y;
-      const PsiT* srow = psi_k + (size_t)y * kCN;
-      float2 v[16];
+      const PsiT* srow = psi_k + (size_t)y * N;
+      float2 v[kR1];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < kR1; ++i) {
         const int x = t + 8 * i;
         const float2 po = cmul(__ldg(prow + x), __ldg(orow + x));
         const float2 s = psi_ldcs(srow + x);
         v[i] = make_float2(fmaf(2.f, po.x, -s.x), fmaf(2.f, po.y, -s.y));
       }
-      line_dft<false>(v, t, tw, F, [&](int p) { return fidx(y, p); });
+      line_dft<N, false>(v, t, tw, F, [&](int p) { return fidx<N>(y, p); });
 #pragma unroll
-      for (int d = 0; d < 2; ++d)
+      for (int d = 0; d < C::kD; ++d)
 #pragma unroll
-        for (int k2 = 0; k2 < 8; ++k2) F[fidx(y, t + 8 * d + 16 * k2)] = v[p2_index<kCN>(d, k2)];
+        for (int k2 = 0; k2 < 8; ++k2) F[fidx<N>(y, out_pos<N>(t, d, k2))] = v[p2_index<N>(d, k2)];
     }
     __syncthreads();
 
@@ -206,18 +225,18 @@ __global__ void __launch_bounds__(kCT, 1) k_fourier_cluster(const __grid_constan
 #pragma unroll 1
     for (int rho = 0; rho < 2; ++rho) {
       const int c = g + kCGroups * rho;
-      float2 v[16];
+      float2 v[kR1];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = F[fidx(t + 8 * i, c)];
-      line_dft<false>(v, t, tw, F, [&](int p) { return fidx(p, c); });
+      for (int i = 0; i < kR1; ++i) v[i] = F[fidx<N>(t + 8 * i, c)];
+      line_dft<N, false>(v, t, tw, F, [&](int p) { return fidx<N>(p, c); });
 #pragma unroll
-      for (int d = 0; d < 2; ++d)
+      for (int d = 0; d < C::kD; ++d)
 #pragma unroll
         for (int k2 = 0; k2 < 8; ++k2) {
-          const int q = t + 8 * d + 16 * k2;
-          const float2 X = v[p2_index<kCN>(d, k2)];
-          F[fidx(q, c)] = X;
-          NB[nidx(q, c)] = cnorm(X);
+          const int q = out_pos<N>(t, d, k2);
+          const float2 X = v[p2_index<N>(d, k2)];
+          F[fidx<N>(q, c)] = X;
+          NB[nidx<N>(q, c)] = cnorm(X);
         }
     }
     cluster_sync();   // A: every mode's norms are in place
@@ -228,7 +247,7 @@ __global__ void __launch_bounds__(kCT, 1) k_fourier_cluster(const __grid_constan
     float ef = 0.f;
     const float* inten = a.istrip + (size_t)j * kCPix;   // strip order, as p below
     for (int p = plo + 4 * tid; p < phi; p += 4 * kCT) {
-      const uint32_t off = 4u * (uint32_t)nidx_strip(p);
+      const uint32_t off = 4u * (uint32_t)nidx_strip<N>(p);
       float4 S = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int k = 0; k < M; ++k) {
         const float4 n = ld_dsmem4(dsmem_addr(nb_s + off, (uint32_t)k));
@@ -259,17 +278,17 @@ __global__ void __launch_bounds__(kCT, 1) k_fourier_cluster(const __grid_constan
 #pragma unroll 1
     for (int rho = 0; rho < 2; ++rho) {
       const int c = g + kCGroups * rho;
-      float2 v[16];
+      float2 v[kR1];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < kR1; ++i) {
         const int q = t + 8 * i;
-        v[i] = cscale(F[fidx(q, c)], NB[nidx(q, c)]);
+        v[i] = cscale(F[fidx<N>(q, c)], NB[nidx<N>(q, c)]);
       }
-      line_dft<true>(v, t, tw, F, [&](int p) { return fidx(p, c); });
+      line_dft<N, true>(v, t, tw, F, [&](int p) { return fidx<N>(p, c); });
 #pragma unroll
-      for (int d = 0; d < 2; ++d)
+      for (int d = 0; d < C::kD; ++d)
 #pragma unroll
-        for (int k2 = 0; k2 < 8; ++k2) F[fidx(t + 8 * d + 16 * k2, c)] = v[p2_index<kCN>(d, k2)];
+        for (int k2 = 0; k2 < 8; ++k2) F[fidx<N>(out_pos<N>(t, d, k2), c)] = v[p2_index<N>(d, k2)];
     }
     __syncthreads();
 
@@ -277,24 +296,24 @@ __global__ void __launch_bounds__(kCT, 1) k_fourier_cluster(const __grid_constan
 #pragma unroll 1
     for (int rho = 0; rho < 2; ++rho) {
       const int y = group_row(g) + kCGroups * rho;
-      const float2* prow = P_k + (size_t)y * kCN;
+      const float2* prow = P_k + (size_t)y * N;
       const float2* orow = a.obj + (size_t)(pos.x + y) * a.W + pos.y;
-      PsiT* srow = static_cast<PsiT*>(a.psi) + ((size_t)j * M + r) * kCPix + (size_t)y * kCN;
-      float2 v[16];
+      PsiT* srow = static_cast<PsiT*>(a.psi) + ((size_t)j * M + r) * kCPix + (size_t)y * N;
+      float2 v[kR1];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = F[fidx(y, t + 8 * i)];
-      line_dft<true>(v, t, tw, F, [&](int p) { return fidx(y, p); });
+      for (int i = 0; i < kR1; ++i) v[i] = F[fidx<N>(y, t + 8 * i)];
+      line_dft<N, true>(v, t, tw, F, [&](int p) { return fidx<N>(y, p); });
 #pragma unroll
-      for (int d = 0; d < 2; ++d)
+      for (int d = 0; d < C::kD; ++d)
 #pragma unroll
         for (int k2 = 0; k2 < 8; ++k2) {
-          const int x = t + 8 * d + 16 * k2;
+          const int x = out_pos<N>(t, d, k2);
           const float2 pk = __ldg(prow + x);
           const float2 po = cmul(pk, __ldg(orow + x));
-          const float2 g2 = v[p2_index<kCN>(d, k2)];
+          const float2 g2 = v[p2_index<N>(d, k2)];
           const float2 pn = make_float2(fmaf(c2b, po.x, g2.x), fmaf(c2b, po.y, g2.y));
           psi_stcs(srow + x, pn);
-          F[fidx(y, x)] = cconjmul(pk, pn);
+          F[fidx<N>(y, x)] = cconjmul(pk, pn);
         }
     }
     cluster_sync();   // C: every mode's conj(P_k) psi'_k is in place
@@ -302,8 +321,8 @@ __global__ void __launch_bounds__(kCT, 1) k_fourier_cluster(const __grid_constan
     // ---- 6: object source c_j of this CTA's pixels (two per thread) ----
     float2* cv = a.cview + (size_t)j * kCPix;
     for (int pp = qlo + tid; pp < qhi; pp += kCT) {
-      const int px = 2 * pp, q = px >> 7, x = px & (kCN - 1);
-      const uint32_t off = 8u * (uint32_t)fidx(q, x);   // x even: the pair is one 16-byte chunk
+      const int px = 2 * pp, q = px / N, x = px & (N - 1);
+      const uint32_t off = 8u * (uint32_t)fidx<N>(q, x);   // x even: the pair is one 16-byte chunk
       float4 acc = ld_dsmem4(dsmem_addr(f_s + off, 0));
       for (int k = 1; k < M; ++k) {
         const float4 u = ld_dsmem4(dsmem_addr(f_s + off, (uint32_t)k));
@@ -317,18 +336,18 @@ __global__ void __launch_bounds__(kCT, 1) k_fourier_cluster(const __grid_constan
   }
 }
 
-template <class PsiT>
+template <int N, class PsiT>
 cudaError_t set_cluster_attrs() {
-  return cudaFuncSetAttribute(k_fourier_cluster<PsiT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)fourier_cluster_smem_bytes());
+  return cudaFuncSetAttribute(k_fourier_cluster<N, PsiT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)fourier_cluster_smem_bytes(N));
 }
 
-template <class PsiT>
+template <int N>
 cudaLaunchConfig_t cluster_config(int nclusters, int M, cudaStream_t s, cudaLaunchAttribute* at) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nclusters * M));
-  cfg.blockDim = dim3(kCT);
-  cfg.dynamicSmemBytes = fourier_cluster_smem_bytes();
+  cfg.blockDim = dim3(CShape<N>::kT);
+  cfg.dynamicSmemBytes = fourier_cluster_smem_bytes(N);
   cfg.stream = s;
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = (unsigned)M;
@@ -339,26 +358,42 @@ cudaLaunchConfig_t cluster_config(int nclusters, int M, cudaStream_t s, cudaLaun
   return cfg;
 }
 
-}  // namespace
-
-size_t fourier_cluster_smem_bytes() { return kFrameBytes + kNormBytes + kTwCBytes; }
-
-int fourier_cluster_capacity(int M) {
-  if (M < 1 || M > kClusterMaxModes) return 0;
-  if (set_cluster_attrs<float2>() != cudaSuccess || set_cluster_attrs<__half2>() != cudaSuccess) return 0;
+template <int N>
+int capacity(int M) {
+  if (set_cluster_attrs<N, float2>() != cudaSuccess || set_cluster_attrs<N, __half2>() != cudaSuccess) return 0;
   cudaLaunchAttribute at[1];
-  const cudaLaunchConfig_t cfg = cluster_config<float2>(1, M, 0, at);
+  const cudaLaunchConfig_t cfg = cluster_config<N>(1, M, 0, at);
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_fourier_cluster<float2>, &cfg) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_fourier_cluster<N, float2>, &cfg) != cudaSuccess) return 0;
   return n;
 }
 
-cudaError_t launch_fourier_cluster(const FourierArgs& a, int nclusters, cudaStream_t s) {
-  if (a.N != kCN || a.M < 1 || a.M > kClusterMaxModes || nclusters < 1) return cudaErrorInvalidValue;
+template <int N>
+cudaError_t launch(const FourierArgs& a, int nclusters, cudaStream_t s) {
   cudaLaunchAttribute at[1];
-  const cudaLaunchConfig_t cfg = cluster_config<float2>(nclusters, a.M, s, at);
-  if (a.psi16) return cudaLaunchKernelEx(&cfg, k_fourier_cluster<__half2>, a);
-  return cudaLaunchKernelEx(&cfg, k_fourier_cluster<float2>, a);
+  const cudaLaunchConfig_t cfg = cluster_config<N>(nclusters, a.M, s, at);
+  if (a.psi16) return cudaLaunchKernelEx(&cfg, k_fourier_cluster<N, __half2>, a);
+  return cudaLaunchKernelEx(&cfg, k_fourier_cluster<N, float2>, a);
+}
+
+}  // namespace
+
+bool fourier_cluster_shape(int N, int M) { return (N == 64 || N == 128) && M >= 1 && M <= kClusterMaxModes; }
+
+size_t fourier_cluster_smem_bytes(int N) {
+  if (N == 128) return CShape<128>::kFrameBytes + CShape<128>::kNormBytes + CShape<128>::kTwBytes;
+  if (N == 64) return CShape<64>::kFrameBytes + CShape<64>::kNormBytes + CShape<64>::kTwBytes;
+  return 0;
+}
+
+int fourier_cluster_capacity(int N, int M) {
+  if (!fourier_cluster_shape(N, M)) return 0;
+  return N == 128 ? capacity<128>(M) : capacity<64>(M);
+}
+
+cudaError_t launch_fourier_cluster(const FourierArgs& a, int nclusters, cudaStream_t s) {
+  if (!fourier_cluster_shape(a.N, a.M) || nclusters < 1) return cudaErrorInvalidValue;
+  return a.N == 128 ? launch<128>(a, nclusters, s) : launch<64>(a, nclusters, s);
 }
 
 }  // namespace dmk

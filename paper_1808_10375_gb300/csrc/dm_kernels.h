@@ -84,19 +84,19 @@ int fourier_split_occupancy(size_t smem);
 // isplit[j][k1][x][k2] = inten[j][k1 + 16 k2][x] (J views of 256 x 256)
 cudaError_t launch_intensity_split(float* isplit, const float* inten, int J, cudaStream_t s);
 
-// The cluster form of the Fourier step (dm_fourier_cluster.cu) for 128 x 128
-// frames and 1 to 8 modes: one thread-block cluster per view and one CTA per
-// mode, each holding its mode's whole frame in shared memory; the mode sums
-// are reduce-scatters over distributed shared memory.  It uses no scratch
-// ring, counters or tensor maps; views go to clusters round-robin.  It
-// writes ef_part[j * M + mode] (M partials per view) and does not track the
-// exit-wave change (psi_part).
-constexpr int kClusterN = 128;
+// The cluster form of the Fourier step (dm_fourier_cluster.cu) for 64 x 64
+// and 128 x 128 frames and 1 to 8 modes: one thread-block cluster per view
+// and one CTA per mode, each holding its mode's whole frame in shared memory;
+// the mode sums are reduce-scatters over distributed shared memory.  It uses
+// no scratch ring, counters or tensor maps; views go to clusters round-robin.
+// It writes ef_part[j * M + mode] (M partials per view) and does not track
+// the exit-wave change (psi_part).
 constexpr int kClusterMaxModes = 8;
-size_t fourier_cluster_smem_bytes();
+bool fourier_cluster_shape(int N, int M);   // whether the form exists for N x N frames and M modes
+size_t fourier_cluster_smem_bytes(int N);
 // clusters of M CTAs resident at once (0: the form cannot run); also sets the
 // kernels' shared-memory limit, so it runs once before the first launch
-int fourier_cluster_capacity(int M);
+int fourier_cluster_capacity(int N, int M);
 cudaError_t launch_fourier_cluster(const FourierArgs& a, int nclusters, cudaStream_t s);
 
 // Several scans of one frame size in one persistent Fourier launch: scan s

@@ -1,5 +1,5 @@
-"""GPU parity of the cluster form of the Fourier step (128 x 128 frames, 1 to
-8 modes), through the C ABI against the FP64 oracle: one and three
+"""GPU parity of the cluster form of the Fourier step (64 x 64 and 128 x 128
+frames, 1 to 8 modes), through the C ABI against the FP64 oracle: one and three
 iterations, more views than resident clusters (several views per cluster),
 footprints at the object edges, one mode and eight, and agreement with the
 strip form to FP32 rounding.  Both forms compute Eq. 3 with the constrained
@@ -26,15 +26,18 @@ def _dm():
     return dm
 
 
-@pytest.mark.parametrize("modes,grid,obj,seed", [
-    (4, (3, 3), (170, 175), 41),
-    (1, (3, 2), (170, 155), 42),
-    (3, (2, 3), (160, 170), 43),
-    (8, (3, 3), (170, 175), 44),
+@pytest.mark.parametrize("n,modes,grid,step,obj,seed", [
+    (128, 4, (3, 3), 18, (170, 175), 41),
+    (128, 1, (3, 2), 18, (170, 155), 42),
+    (128, 3, (2, 3), 18, (160, 170), 43),
+    (128, 8, (3, 3), 18, (170, 175), 44),
+    (64, 4, (4, 4), 10, (100, 100), 52),
+    (64, 1, (3, 4), 9, (86, 95), 53),
+    (64, 8, (3, 3), 12, (92, 92), 54),
 ])
-def test_cluster_form_matches_oracle(modes, grid, obj, seed):
+def test_cluster_form_matches_oracle(n, modes, grid, step, obj, seed):
     dm = _dm()
-    s, p0, o0, psi0 = case(128, modes, grid, 18, obj, seed, probe="hg")
+    s, p0, o0, psi0 = case(n, modes, grid, step, obj, seed, probe="hg")
     g = run_gpu(s, p0, o0, psi0, form=dm.DM_FOURIER_CLUSTER)
     o = run_oracle(s, p0, o0, psi0)
     compare(g, o)
@@ -48,6 +51,21 @@ def test_cluster_form_more_views_than_clusters_and_edges():
     s, p0, o0, psi0 = case(n, m, (7, 6), 12, (200, 188), 45, jitter=0, probe="hg")
     h, w = s.obj_shape
     assert s.views == 42
+    assert s.pos[:, 0].min() == 0 and s.pos[:, 0].max() == h - n
+    assert s.pos[:, 1].min() == 0 and s.pos[:, 1].max() == w - n
+    g = run_gpu(s, p0, o0, psi0, form=dm.DM_FOURIER_CLUSTER)
+    o = run_oracle(s, p0, o0, psi0)
+    compare(g, o)
+
+
+def test_cluster_form_64_more_views_than_clusters_and_edges():
+    # 64 x 64 frames, 8 modes: 400 views are several per resident cluster;
+    # footprints touch all four object edges
+    dm = _dm()
+    n, m = 64, 8
+    s, p0, o0, psi0 = case(n, m, (20, 20), 4, (140, 140), 55, jitter=0, probe="hg")
+    h, w = s.obj_shape
+    assert s.views == 400
     assert s.pos[:, 0].min() == 0 and s.pos[:, 0].max() == h - n
     assert s.pos[:, 1].min() == 0 and s.pos[:, 1].max() == w - n
     g = run_gpu(s, p0, o0, psi0, form=dm.DM_FOURIER_CLUSTER)
@@ -78,7 +96,7 @@ def test_cluster_and_strip_agree_to_fp32_rounding():
 def test_cluster_form_selection_rules():
     dm = _dm()
     # other shapes have no cluster form
-    for n, m, obj in ((256, 8, (290, 290)), (64, 2, (110, 110)), (128, 9, (170, 170))):
+    for n, m, obj in ((256, 8, (290, 290)), (32, 2, (60, 60)), (128, 9, (170, 170)), (64, 9, (95, 95))):
         s, p0, o0, psi0 = case(n, m, (2, 2), 24, obj, 48, probe="hg")
         h, w = s.obj_shape
         params = dm.dm_params_default(n=n, modes=m, views=s.views, obj_h=h, obj_w=w)
