@@ -55,7 +55,7 @@ struct CShape {
   static constexpr size_t kFrameBytes = sizeof(float2) * kPix;   // 128 or 32 KB
   static constexpr size_t kNormBytes = sizeof(float) * kPix;     // 64 or 16 KB
   static constexpr size_t kTwBytes = sizeof(float2) * N;         // W_N^(t k1), t < 8, k1 < R1
-  static constexpr int kMinBlocks = N == 128 ? 1 : 3;            // CTAs per SM the registers allow
+  static constexpr int kMinBlocks = N == 128 ? 1 : 4;            // CTAs per SM the registers allow
   static_assert(FftShape<N>::R2 == 8 && (kR1 == 16 || kR1 == 8), "8-lane lines of 64 or 128 points");
   static_assert(N == 2 * kGroups, "each group takes two lines per pass");
 };
