@@ -284,8 +284,8 @@ int dm_autotune(dm_ctx* ctx, int32_t sample_views, double* best_ms);
  * column task's two item lanes. */
 int dm_get_plan(const dm_ctx* ctx, int64_t* out);
 
-/* Two forms of the Fourier step (Eq. 3 with the constrained transform F_c of
- * Sec. II); both compute the same iteration to FP32 rounding.
+/* Three forms of the Fourier step (Eq. 3 with the constrained transform F_c
+ * of Sec. II); all compute the same iteration to FP32 rounding.
  * DM_FOURIER_STRIP: row tasks take the row DFTs, column tasks the column
  * DFTs, the modulus projection and the inverse column DFTs of 2-column
  * strips of all modes; every frame size, mode count and exit-wave storage.
@@ -295,7 +295,7 @@ int dm_get_plan(const dm_ctx* ctx, int64_t* out);
  * tasks, whose work items are 16 columns x 16 rows x 8 modes; the mode sum
  * of F_c is then a warp-shuffle reduction.  It keeps the intensities in a
  * second layout as well (4 N^2 bytes more per view).  The exit-wave change
- * (dm_set_psi_error) and dm_batch iterations run the strip form.  The split
+ * (dm_set_psi_error) and dm_batch iterations run the strip form instead.  The split
  * form has a scratch ring of its own (160 MiB of 5 slots by default: more
  * views in flight let its tasks overlap more; dm_params.scratch_bytes, when
  * set, sizes both forms' rings).  Contexts that can run the split form start with it; dm_autotune
